@@ -1,0 +1,337 @@
+"""Benchmark of the V-family generation path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Workload (default): V-MT19937-32 with 16 lanes, 65536 independent generators
+seeded from splitmix64(1); one step produces 2^30 uint32 followed by 2^30
+float32 (24-bit conversion) from the running streams, i.e. 16384 + 16384
+outputs per generator, fused into one launch.  The generators are created and
+de-phased (seed + jump-ahead) before the timed region; their states stay
+resident in HBM.  Every step writes 8 GiB, far more than the 129 MB L2, so no
+flush is needed between steps.
+
+The JSON line reports random GB/s written (output bytes / device time), the
+HBM roofline of the generation kernel (algorithmic bytes = output + one read
+and one write of every combined state), the end-to-end rate through the C ABI
+into pinned host memory, the one-time initialisation cost and the oracle on
+the host cores.  Under torchrun every rank runs the full per-GPU workload with
+its own seeds (weak scaling); the max time over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2309_16682_gb300 import inputs as I  # noqa: E402
+
+METRIC = "random GB/s written (bit-exact)"
+UNIT = "GB/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# oracle legs (host cores)
+# ---------------------------------------------------------------------------
+_POOL = {}
+
+
+def _oracle_pool(workload: str, pool: int = 4):
+    """Lane states of the first `pool` generators of the workload (oracle)."""
+    import oracle as O
+    if workload not in _POOL:
+        w = I.WORKLOADS[workload]
+        v = O.VARIANTS[w["variant"]]
+        seeds = I.workload_seeds(workload)
+        t0 = time.perf_counter()
+        lanes = [O.lane_states(v, w["lanes"], int(seeds[g])) for g in range(pool)]
+        _POOL[workload] = (lanes, time.perf_counter() - t0, pool)
+    return _POOL[workload]
+
+
+def oracle_sample(workload: str, min_seconds: float, max_gens: int = 1 << 20):
+    """Time the oracle producing whole per-generator step outputs (all segments,
+    interleave and conversion) until min_seconds have passed.  The lane states
+    come from a small pool prepared before timing; generation cost does not
+    depend on which state is used.  Returns (bytes, seconds, generators)."""
+    import oracle as O
+    w = I.WORKLOADS[workload]
+    v = O.VARIANTS[w["variant"]]
+    count = w["generators"]
+    segs = [(n // count, dt) for dt, n in w["outputs"]]
+    words = sum(n * O.words_per_output(v, dt) for n, dt in segs)
+    lanes, _, pool = _oracle_pool(workload)
+    t0 = time.perf_counter()
+    nbytes, gens = 0, 0
+    while gens < max_gens:
+        ws = O.vstream_words(v, w["lanes"], 0, words, 0, lanes=lanes[gens % pool])
+        off = 0
+        for n, dt in segs:
+            k = n * O.words_per_output(v, dt)
+            nbytes += O.convert(v, ws[off:off + k], dt).nbytes
+            off += k
+        gens += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    return nbytes, time.perf_counter() - t0, gens
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle as O
+    O.prepare_all()
+    w = I.WORKLOADS[args.workload]
+    _oracle_pool(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, 0.0, max_gens=1)
+    tot_b, tot_t, tot_g = 0, 0.0, 0
+    for _ in range(args.steps):
+        b, t, gens = oracle_sample(args.workload, args.ref_seconds / max(args.steps, 1))
+        tot_b += b
+        tot_t += t
+        tot_g += gens
+    val = tot_b / tot_t / 1e9
+    sample = (f"{tot_g} whole per-generator step outputs ({tot_b} bytes) of the {w['generators']}-generator "
+              f"workload over {args.steps} steps; lane states from a pool of 4 generators prepared untimed")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": args.workload},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------
+def run_gb300(args, world, rank, local):
+    import torch
+    import paper_2309_16682_gb300 as vmt
+    w = I.WORKLOADS[args.workload]
+    count = w["generators"]
+    segs = [(n // count, dt) for dt, n in w["outputs"]]
+    esize = {"u32": 4, "f32": 4, "u64": 8, "f64": 8}
+    out_bytes = sum(n * count * esize[dt] for n, dt in segs)
+    seeds = I.workload_seeds(args.workload)
+    if rank:
+        seeds = I.splitmix64(1000003 * rank + 1, count)  # each rank: its own generators
+    stream = torch.cuda.current_stream()
+
+    # one-time initialisation: seeding + jump-ahead de-phasing (timed separately)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = vmt.VGenerator(w["variant"], w["lanes"], seeds)
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    from paper_2309_16682_gb300 import UNITS
+    unit_bytes = {"mt32": 4, "mt64": 8, "sfmt": 16}[w["variant"]]
+    state_bytes = count * w["lanes"] * UNITS[vmt.VARIANTS[w["variant"]]] * unit_bytes
+    outs = [torch.empty((count, n), dtype=vmt._torch_dtype(dt), device="cuda") for n, dt in segs]
+
+    def step():
+        g.generate_multi(segs, outs=outs)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for k in range(args.steps):
+        step()
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(world)
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    total_ms = max_over_ranks(world, total_ms)
+    value = out_bytes * args.steps * world / (total_ms / 1e3) / 1e9
+    # the step is one kernel launch: its average duration is the step time
+    launch_ms = float(np.mean(per_step))
+    alg_bytes = out_bytes + 2 * state_bytes
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+
+    # end to end through the C ABI into pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        hosts = [torch.empty((count, n), dtype=vmt._torch_dtype(dt), pin_memory=True) for n, dt in segs]
+        for hb, (n, dt) in zip(hosts, segs):   # warm-up
+            g.generate_host(n, dt, out=hb)
+        barrier(world)
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            for hb, (n, dt) in zip(hosts, segs):
+                g.generate_host(n, dt, out=hb)
+        e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+        e2e = {"value": out_bytes * e2e_steps * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": out_bytes, "steps": e2e_steps}
+        del hosts
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle as O
+        O.prepare_all()
+        _, t_pool, pool = _oracle_pool(args.workload)
+        b, t, gens = oracle_sample(args.workload, args.ref_seconds)
+        cpu = {"value": b / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{gens} whole per-generator step outputs ({b} bytes) in {t:.1f} s on one core; "
+                         f"seed+jump of {pool} generators took {t_pool:.1f} s"}
+
+    if rank == 0:
+        lane_jumps = count * w["lanes"]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "variant": w["variant"], "lanes": w["lanes"],
+                       "generators_per_gpu": count, "outputs_per_step": [[dt, n * count] for n, dt in segs],
+                       "l2": "no flush: each step writes %.1f GiB (> 129 MB L2)" % (out_bytes / 2**30),
+                       "parallelism": f"{world} independent GPU(s), generators sharded, no collective"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "output_only_frac": out_bytes / (launch_ms / 1e3) / 1e9 / peak,
+                         "kernel": "gen_mt_kernel<MT32,16,4,512>"},
+            "gpu_launches": args.steps,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "init": {"seconds": init_s, "lane_jumps": lane_jumps, "lane_jumps_per_s": lane_jumps / init_s,
+                     "note": "seed + jump-ahead de-phasing before the timed region (first call also loads or "
+                             "computes the jump polynomials)"},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="vmt32_m16_g65536", choices=sorted(I.WORKLOADS))
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gb300(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

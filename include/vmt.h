@@ -1,0 +1,182 @@
+/*
+ * vmt.h -- C ABI of the GB300 V-family generator library (libvmt.so).
+ *
+ * The V-family of arXiv 2309.16682 ("VMT19937: A SIMD-Friendly Pseudo Random
+ * Number Generator based on Mersenne Twister 19937"), Sec. 3: M instances of a
+ * base generator (MT19937-32, MT19937-64 or SFMT19937) are de-phased by
+ * jump-ahead so that lane t starts J = ceil(P/M) = 2^(19937 - log2 M) steps
+ * after lane t-1 (Table "jvalues"), and their outputs are polled round robin
+ * into one stream S (eq. combseq): S[kM + t] = z_{tJ + k}.  For SFMT19937 the
+ * interleave unit is the 128-bit element, emitted as four 32-bit words,
+ * least-significant sub-word first.
+ *
+ * Conventions for every call:
+ *   - return 0 (VMT_OK) or a negative VMT_E* code; vmt_last_error() gives a
+ *     thread-local message for the last failure on the calling thread;
+ *   - `cuda_stream` is a cudaStream_t (NULL = legacy default stream); device
+ *     work is enqueued on it and the call returns without synchronising unless
+ *     the call's description says otherwise;
+ *   - a vmt_state owns its device memory until vmt_free(); device pointers
+ *     passed in (out_dev) are owned by the caller;
+ *   - all generators of one vmt_state advance in lock-step: every generate call
+ *     takes the same number of words from each of them.
+ *
+ * Words: "native words" are 32-bit for MT19937-32 and SFMT19937 and 64-bit for
+ * MT19937-64.  Output types and the words they consume:
+ *   VMT_U32  one 32-bit word                 (not defined for MT19937-64)
+ *   VMT_U64  a | b << 32 from two 32-bit words a, b (32-bit variants), or one
+ *            64-bit word
+ *   VMT_F32  (z >> 8) * 2^-24 from a 32-bit word, (z >> 40) * 2^-24 from a
+ *            64-bit word; in [0, 1), exact
+ *   VMT_F64  ((a >> 5) * 2^26 + (b >> 6)) * 2^-53 from two 32-bit words, or
+ *            (z >> 11) * 2^-53 from a 64-bit word; in [0, 1), exact
+ * The conversions are not in the paper; they are the usual 24/53-bit forms.
+ */
+#ifndef VMT_H
+#define VMT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* base generators (Sec. 2.2, 2.3, 2.4) */
+#define VMT_MT19937_32 0
+#define VMT_MT19937_64 1
+#define VMT_SFMT19937 2
+
+/* output types */
+#define VMT_U32 0
+#define VMT_U64 1
+#define VMT_F32 2
+#define VMT_F64 3
+
+/* status codes */
+#define VMT_OK 0
+#define VMT_EINVAL (-1)   /* bad argument (variant, lanes, dtype, size, pointer) */
+#define VMT_ENOMEM (-2)   /* device or host allocation failed */
+#define VMT_ECUDA (-3)    /* a CUDA runtime call failed */
+#define VMT_ETIMEOUT (-4) /* a bounded wait ran out */
+#define VMT_EBUSY (-5)    /* resource in use / admission refused */
+#define VMT_ESTATE (-6)   /* corrupt or mismatching exported state */
+
+typedef struct vmt_state vmt_state;
+
+/*
+ * vmt_init -- create one V-family generator (Sec. 3, construction of the
+ * V generator; Sec. 3.1, initialisation by jump-ahead).
+ *   st        out: the new generator (free with vmt_free)
+ *   variant   VMT_MT19937_32, VMT_MT19937_64 or VMT_SFMT19937
+ *   lanes     M in {1, 2, 4, 8, 16}
+ *   seed      base-generator seed (32-bit variants use seed mod 2^32); seeding
+ *             follows the C++ standard's mersenne_twister_engine recurrence,
+ *             SFMT19937 adds its period certification
+ *   jump      offset d applied to the base state before de-phasing: lane t
+ *             starts at z_{d + tJ}
+ * The first call for a variant in a process computes (or loads from the
+ * on-disk cache) the variant's minimal polynomial and jump polynomials; this
+ * takes seconds once and synchronises `cuda_stream`.
+ */
+int vmt_init(vmt_state** st, int variant, int lanes, uint64_t seed, uint64_t jump, void* cuda_stream);
+
+/*
+ * vmt_init_batch -- `count` independent V-family generators in one state
+ * object (same variant and M).  seeds[g] and jumps[g] (host arrays, copied;
+ * jumps may be NULL for all-zero) set generator g as in vmt_init.  Seeding,
+ * jump-ahead and lane de-phasing run as batched kernels.
+ */
+int vmt_init_batch(vmt_state** st, int variant, int lanes, int64_t count, const uint64_t* seeds,
+                   const uint64_t* jumps, void* cuda_stream);
+
+/*
+ * vmt_jump -- apply the jump polynomial c(F) to every lane of every generator
+ * (Sec. 3.1).  poly: host array of ceil(nbits/64) words, bit i of word i/64 is
+ * the coefficient of x^i; nbits <= 20480.  A polynomial congruent to x^d
+ * modulo the minimal polynomial advances every lane by d steps.
+ */
+int vmt_jump(vmt_state* st, const uint64_t* poly, int64_t nbits, void* cuda_stream);
+
+/*
+ * vmt_jump_poly -- write x^(d * 2^log2_extra) mod mu into poly_out (host,
+ * cap_words uint64 words).  mu is the variant's minimal polynomial.  Returns
+ * the number of words written, or a negative status.  With d = 1 and
+ * log2_extra = 19937 - log2 M it gives the lane spacing J of Table "jvalues".
+ */
+int vmt_jump_poly(int variant, uint64_t d, int log2_extra, uint64_t* poly_out, int64_t cap_words);
+
+/*
+ * vmt_generate -- the next n outputs of type dtype from every generator.
+ * Generator g writes out_dev[g*n .. g*n + n) (device memory, caller-owned,
+ * at least count*n elements).  The stream continues across calls: a call
+ * resumes exactly at the next word of S.  n >= 0.
+ */
+int vmt_generate(vmt_state* st, int64_t n, int dtype, void* out_dev, void* cuda_stream);
+
+/*
+ * vmt_generate_multi -- several consecutive output segments in one pass:
+ * segment i takes counts[i] outputs of type dtypes[i] from the stream, and
+ * generator g writes them at outs[i] + g*counts[i] elements.  Equivalent to
+ * nseg consecutive vmt_generate calls; 1 <= nseg <= 4.
+ */
+int vmt_generate_multi(vmt_state* st, int nseg, const int64_t* counts, const int* dtypes, void* const* outs,
+                       void* cuda_stream);
+
+/*
+ * vmt_generate_host -- as vmt_generate but into host memory (pinned or
+ * pageable): the words are generated into a device staging buffer in chunks
+ * and copied to out_host, generation of one chunk overlapping the copy of the
+ * previous one.  Synchronises `cuda_stream` before returning.
+ */
+int vmt_generate_host(vmt_state* st, int64_t n, int dtype, void* out_host, void* cuda_stream);
+
+/* Bytes of an exported state (header + all generators' states). */
+int64_t vmt_state_bytes(const vmt_state* st);
+
+/*
+ * vmt_state_export / vmt_state_import -- checkpoint of every generator's
+ * combined state X-hat (Sec. 3) and stream position.  export writes
+ * vmt_state_bytes(st) bytes to host_buf (cap bytes available) and
+ * synchronises; import overwrites a state object of the same variant, lanes
+ * and count (VMT_ESTATE on mismatch).  A generator resumed from an export
+ * continues the stream exactly.
+ */
+int vmt_state_export(const vmt_state* st, void* host_buf, size_t cap, void* cuda_stream);
+int vmt_state_import(vmt_state* st, const void* host_buf, size_t len, void* cuda_stream);
+
+/* Variant, lanes M, generator count and current block position of a state. */
+int vmt_state_info(const vmt_state* st, int* variant, int* lanes, int64_t* count, int64_t* block_pos);
+
+/* Device pointer of the combined states ([count][n][M] units) -- for tests. */
+void* vmt_state_device_ptr(const vmt_state* st);
+
+/* Release a state object (NULL is allowed). */
+void vmt_free(vmt_state* st);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* vmt_last_error(void);
+
+/* Directory of the on-disk cache of minimal/jump polynomials (NULL: default). */
+int vmt_set_cache_dir(const char* path);
+
+/*
+ * Host polynomial helpers (no GPU needed): Berlekamp-Massey, products modulo a
+ * polynomial and the chain x^(2^q) mod mu, as used to build jump polynomials
+ * (Sec. 3.1).  All polynomials are uint64 word arrays, bit i = coefficient of
+ * x^i.
+ *   vmt_poly_minpoly   bits: n sequence bits packed little-endian; writes
+ *                      mu (cap_words) and returns deg mu (linear complexity)
+ *   vmt_poly_mulmod    out = a * b mod mu (all nw words)
+ *   vmt_poly_x2pow     out[i] = x^(2^(q_lo + i)) mod mu for q_lo <= q <= q_hi,
+ *                      nw words per entry
+ */
+int vmt_poly_minpoly(const uint64_t* bits, int64_t n, uint64_t* mu_out, int64_t cap_words);
+int vmt_poly_mulmod(const uint64_t* a, const uint64_t* b, const uint64_t* mu, uint64_t* out, int64_t nw);
+int vmt_poly_x2pow(const uint64_t* mu, int64_t nw, int q_lo, int q_hi, uint64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VMT_H */

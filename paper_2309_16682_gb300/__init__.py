@@ -1,0 +1,225 @@
+"""GB300-native V-family generators (arXiv 2309.16682): Python binding.
+
+A thin ctypes layer over the C ABI of ``_build/libvmt.so`` (declared in
+``include/vmt.h``).  It only marshals arguments: seeding, jump-ahead, twist,
+tempering, interleave, conversion and stores all run in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library is missing the calls raise.
+
+    >>> import torch, paper_2309_16682_gb300 as vmt
+    >>> g = vmt.VGenerator("mt32", lanes=16, seeds=[5489])
+    >>> x = g.generate(1 << 20, "u32")          # torch.uint32 tensor on cuda
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libvmt.so")
+CACHE_DIR = os.path.join(HERE, "_cache")
+
+VARIANTS = {"mt32": 0, "mt64": 1, "sfmt": 2}
+DTYPES = {"u32": 0, "u64": 1, "f32": 2, "f64": 3}
+UNITS = {0: 624, 1: 312, 2: 156}
+
+VMT_OK, VMT_EINVAL, VMT_ENOMEM, VMT_ECUDA, VMT_ETIMEOUT, VMT_EBUSY, VMT_ESTATE = 0, -1, -2, -3, -4, -5, -6
+
+_lib = None
+_lock = threading.Lock()
+
+
+class VMTError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"vmt error {code}: {msg}")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """Load libvmt.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2309_16682_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        sigs = {
+            "vmt_init": (I, [PP, I, I, U64, U64, P]),
+            "vmt_init_batch": (I, [PP, I, I, I64, P, P, P]),
+            "vmt_jump": (I, [P, P, I64, P]),
+            "vmt_jump_poly": (I, [I, U64, I, P, I64]),
+            "vmt_generate": (I, [P, I64, I, P, P]),
+            "vmt_generate_multi": (I, [P, I, P, P, P, P]),
+            "vmt_generate_host": (I, [P, I64, I, P, P]),
+            "vmt_state_bytes": (I64, [P]),
+            "vmt_state_export": (I, [P, P, ctypes.c_size_t, P]),
+            "vmt_state_import": (I, [P, P, ctypes.c_size_t, P]),
+            "vmt_state_info": (I, [P, P, P, P, P]),
+            "vmt_state_device_ptr": (P, [P]),
+            "vmt_free": (None, [P]),
+            "vmt_last_error": (ctypes.c_char_p, []),
+            "vmt_set_cache_dir": (I, [ctypes.c_char_p]),
+            "vmt_poly_minpoly": (I, [P, I64, P, I64]),
+            "vmt_poly_mulmod": (I, [P, P, P, P, I64]),
+            "vmt_poly_x2pow": (I, [P, I64, I, I, P]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        os.makedirs(CACHE_DIR, exist_ok=True)
+        L.vmt_set_cache_dir(CACHE_DIR.encode())
+        _lib = L
+        return L
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise VMTError(rc, lib().vmt_last_error().decode(errors="replace"))
+    return rc
+
+
+def _stream_handle(stream=None) -> ctypes.c_void_p:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _np_ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _torch_dtype(dtype: str):
+    import torch
+    return {"u32": torch.uint32, "u64": torch.uint64, "f32": torch.float32, "f64": torch.float64}[dtype]
+
+
+class VGenerator:
+    """``count`` V-family generators (one vmt_state) advancing in lock-step."""
+
+    def __init__(self, variant: str, lanes: int, seeds, jumps=None, stream=None):
+        self.variant = variant
+        self.v = VARIANTS[variant]
+        self.lanes = int(lanes)
+        seeds = np.ascontiguousarray(np.atleast_1d(np.asarray(seeds, dtype=np.uint64)))
+        self.count = int(seeds.size)
+        js = None
+        if jumps is not None:
+            js = np.ascontiguousarray(np.broadcast_to(np.asarray(jumps, dtype=np.uint64), seeds.shape))
+        h = ctypes.c_void_p()
+        _check(lib().vmt_init_batch(ctypes.byref(h), self.v, self.lanes, self.count, _np_ptr(seeds),
+                                    _np_ptr(js) if js is not None else None, _stream_handle(stream)))
+        self._h = h
+
+    # -- generation ---------------------------------------------------------
+    def generate(self, n: int, dtype: str = "u32", out=None, stream=None):
+        """Next n outputs per generator; returns a [count, n] tensor on the device."""
+        import torch
+        if out is None:
+            out = torch.empty((self.count, n), dtype=_torch_dtype(dtype), device="cuda")
+        _check(lib().vmt_generate(self._h, int(n), DTYPES[dtype], ctypes.c_void_p(out.data_ptr()),
+                                  _stream_handle(stream)))
+        return out
+
+    def generate_multi(self, segments, outs=None, stream=None):
+        """segments: [(n, dtype), ...] consecutive outputs fused into one pass."""
+        import torch
+        nseg = len(segments)
+        if outs is None:
+            outs = [torch.empty((self.count, n), dtype=_torch_dtype(dt), device="cuda") for n, dt in segments]
+        counts = (ctypes.c_int64 * nseg)(*[int(n) for n, _ in segments])
+        dts = (ctypes.c_int * nseg)(*[DTYPES[dt] for _, dt in segments])
+        ptrs = (ctypes.c_void_p * nseg)(*[o.data_ptr() for o in outs])
+        _check(lib().vmt_generate_multi(self._h, nseg, counts, dts, ptrs, _stream_handle(stream)))
+        return outs
+
+    def generate_host(self, n: int, dtype: str = "u32", out=None, stream=None):
+        """Next n outputs per generator into host memory (numpy or pinned torch tensor)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.count, n), dtype=_torch_dtype(dtype), pin_memory=True)
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        _check(lib().vmt_generate_host(self._h, int(n), DTYPES[dtype], ctypes.c_void_p(ptr), _stream_handle(stream)))
+        return out
+
+    # -- jump / state ---------------------------------------------------------
+    def jump(self, poly: np.ndarray, nbits: int | None = None, stream=None):
+        poly = np.ascontiguousarray(poly, dtype=np.uint64)
+        nb = int(nbits if nbits is not None else poly.size * 64)
+        _check(lib().vmt_jump(self._h, _np_ptr(poly), nb, _stream_handle(stream)))
+
+    def info(self):
+        v, m = ctypes.c_int(), ctypes.c_int()
+        c, p = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().vmt_state_info(self._h, ctypes.byref(v), ctypes.byref(m), ctypes.byref(c), ctypes.byref(p)))
+        return dict(variant=v.value, lanes=m.value, count=c.value, block_pos=p.value)
+
+    def export_state(self, stream=None) -> bytes:
+        n = _check(lib().vmt_state_bytes(self._h))
+        buf = np.empty(n, np.uint8)
+        _check(lib().vmt_state_export(self._h, _np_ptr(buf), n, _stream_handle(stream)))
+        return buf.tobytes()
+
+    def import_state(self, blob: bytes, stream=None):
+        buf = np.frombuffer(blob, np.uint8).copy()
+        _check(lib().vmt_state_import(self._h, _np_ptr(buf), buf.size, _stream_handle(stream)))
+
+    def device_states(self):
+        """The combined states as a torch uint8 view-copy [count, bytes] (tests)."""
+        import torch
+        n = _check(lib().vmt_state_bytes(self._h))
+        hdr = 48
+        buf = np.empty(n, np.uint8)
+        _check(lib().vmt_state_export(self._h, _np_ptr(buf), n, _stream_handle(None)))
+        return buf[hdr:].reshape(self.count, -1)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vmt_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def jump_poly(variant: str, d: int, log2_extra: int = 0) -> np.ndarray:
+    out = np.zeros(320, np.uint64)
+    n = _check(lib().vmt_jump_poly(VARIANTS[variant], int(d), int(log2_extra), _np_ptr(out), out.size))
+    return out[:n].copy()
+
+
+def poly_minpoly(bits: np.ndarray) -> tuple[int, np.ndarray]:
+    """Berlekamp-Massey on a 0/1 array (host helper of the library)."""
+    b = np.asarray(bits, dtype=np.uint8)
+    packed = np.zeros((b.size + 63) // 64, np.uint64)
+    idx = np.nonzero(b)[0]
+    np.bitwise_or.at(packed, idx // 64, np.left_shift(np.uint64(1), (idx % 64).astype(np.uint64)))
+    mu = np.zeros(packed.size + 2, np.uint64)
+    d = _check(lib().vmt_poly_minpoly(_np_ptr(packed), b.size, _np_ptr(mu), mu.size))
+    return d, mu
+
+
+def poly_mulmod(a: np.ndarray, b: np.ndarray, mu: np.ndarray) -> np.ndarray:
+    nw = mu.size
+    a = np.ascontiguousarray(a[:nw], np.uint64)
+    b = np.ascontiguousarray(b[:nw], np.uint64)
+    mu = np.ascontiguousarray(mu, np.uint64)
+    out = np.zeros(nw, np.uint64)
+    _check(lib().vmt_poly_mulmod(_np_ptr(a), _np_ptr(b), _np_ptr(mu), _np_ptr(out), nw))
+    return out
+
+
+def poly_x2pow(mu: np.ndarray, q_lo: int, q_hi: int) -> np.ndarray:
+    mu = np.ascontiguousarray(mu, np.uint64)
+    out = np.zeros((q_hi - q_lo + 1, mu.size), np.uint64)
+    _check(lib().vmt_poly_x2pow(_np_ptr(mu), mu.size, q_lo, q_hi, _np_ptr(out)))
+    return out

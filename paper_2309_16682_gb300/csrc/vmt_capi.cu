@@ -1,0 +1,790 @@
+// vmt_capi.cu -- the C ABI declared in include/vmt.h.
+//
+// Host-side orchestration only: argument checking, device memory, the jump
+// polynomial tables and kernel launches.  Every step of the generator path
+// (seeding, jump evaluation, twist, tempering, interleave, conversion, store)
+// runs in the CUDA kernels of gen_mt.cu, gen_sfmt.cu and jump.cu; there is no
+// host fallback for any of them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "gf2poly.hpp"
+#include "vmt_internal.hpp"
+
+namespace vmt {
+cudaError_t launch_generate_mt(int variant, int lanes, const GenArgs& a, cudaStream_t s);
+cudaError_t launch_generate_sfmt(int lanes, const GenArgs& a, cudaStream_t s);
+cudaError_t launch_convert(const void* words, long long words_per_gen, int word64, long long gens, long long wbeg,
+                           int dtype, long long count, void* out, cudaStream_t s);
+
+cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, cudaStream_t s)
+{
+    if (variant == VMT_SFMT19937) return launch_generate_sfmt(lanes, a, s);
+    return launch_generate_mt(variant, lanes, a, s);
+}
+}  // namespace vmt
+
+using vmt::gf2::Poly;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                                       \
+    do {                                                                                                     \
+        cudaError_t e_ = (expr);                                                                             \
+        if (e_ != cudaSuccess) return fail(VMT_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool valid_variant(int v) { return v == VMT_MT19937_32 || v == VMT_MT19937_64 || v == VMT_SFMT19937; }
+bool valid_lanes(int m) { return m == 1 || m == 2 || m == 4 || m == 8 || m == 16; }
+int log2i(int m)
+{
+    int l = 0;
+    while ((1 << l) < m) ++l;
+    return l;
+}
+
+// Lane spacing of Table "jvalues": J = 2^(19937 - log2 M).  Rows 0..15 of a
+// variant's device table hold x^(s * 2^19933) mod mu, s = 0..15, so lane t of
+// an M-lane generator uses row t * 16 / M.  Rows 16 .. 16+2040 hold the
+// base-256 digit jumps x^(v * 256^i), i = 0..7, v = 1..255 (row 16 + 255 i + v - 1).
+constexpr int kPeriodExp = 19937;
+constexpr int kLaneRowQ = kPeriodExp - 4;   // J for M = 16
+constexpr int kDigitRows = 8 * 255;
+constexpr int kChainLo = 72;                // x^(2^q), q < 72, kept for d-jumps
+constexpr int kChainHiFrom = kPeriodExp - 8;
+
+struct VariantCtx {
+    std::mutex mu_lock;
+    bool ready = false;
+    bool digits_ready = false;
+    std::unique_ptr<vmt::gf2::Modulus> mod;
+    std::vector<Poly> chain_lo;    // q = 0 .. kChainLo-1
+    std::vector<Poly> chain_hi;    // q = kChainHiFrom .. kPeriodExp
+    std::vector<Poly> lane_rows;   // 16 rows
+    int device = -1;
+    uint32_t* d_table = nullptr;   // [16 + kDigitRows][kPolyWords]
+    std::vector<int> row_deg;      // degree of each device row
+};
+
+VariantCtx g_ctx[3];
+std::mutex g_cache_lock;
+std::string g_cache_dir;
+
+std::string cache_dir()
+{
+    std::lock_guard<std::mutex> lk(g_cache_lock);
+    if (!g_cache_dir.empty()) return g_cache_dir;
+    const char* e = std::getenv("VMT_CACHE_DIR");
+    return e ? std::string(e) : std::string();
+}
+
+// -------------------------------------------------------------------------
+// polynomial tables
+// -------------------------------------------------------------------------
+void to_rows(const Poly& p, uint32_t* row)
+{
+    std::memset(row, 0, sizeof(uint32_t) * vmt::kPolyWords);
+    for (size_t w = 0; w < p.size() && 2 * w + 1 < static_cast<size_t>(vmt::kPolyWords); ++w) {
+        row[2 * w] = static_cast<uint32_t>(p[w]);
+        row[2 * w + 1] = static_cast<uint32_t>(p[w] >> 32);
+    }
+}
+
+struct CacheHeader {
+    char magic[8];
+    int32_t version, variant, deg, nw, nlo, nhi;
+};
+
+bool load_cache(int variant, Poly& mu, std::vector<Poly>& lo, std::vector<Poly>& hi)
+{
+    const std::string dir = cache_dir();
+    if (dir.empty()) return false;
+    const std::string path = dir + "/minpoly_v" + std::to_string(variant) + ".bin";
+    FILE* f = std::fopen(path.c_str(), "rb");
+    if (!f) return false;
+    CacheHeader h{};
+    bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, "VMTPOLY1", 8) == 0 && h.version == 1 &&
+              h.variant == variant && h.nlo == kChainLo && h.nhi == kPeriodExp - kChainHiFrom + 1 && h.nw > 0 &&
+              h.nw < 1024;
+    if (ok) {
+        mu.assign(static_cast<size_t>(h.nw) + 1, 0);
+        ok = std::fread(mu.data(), 8, mu.size(), f) == mu.size();
+        lo.assign(static_cast<size_t>(h.nlo), Poly(static_cast<size_t>(h.nw), 0));
+        hi.assign(static_cast<size_t>(h.nhi), Poly(static_cast<size_t>(h.nw), 0));
+        for (auto& p : lo) ok = ok && std::fread(p.data(), 8, p.size(), f) == p.size();
+        for (auto& p : hi) ok = ok && std::fread(p.data(), 8, p.size(), f) == p.size();
+        ok = ok && vmt::gf2::degree(mu) == h.deg;
+    }
+    std::fclose(f);
+    return ok;
+}
+
+void save_cache(int variant, const Poly& mu, int nw, const std::vector<Poly>& lo, const std::vector<Poly>& hi)
+{
+    const std::string dir = cache_dir();
+    if (dir.empty()) return;
+    const std::string path = dir + "/minpoly_v" + std::to_string(variant) + ".bin";
+    const std::string tmp = path + ".tmp" + std::to_string(reinterpret_cast<uintptr_t>(&lo));
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    CacheHeader h{};
+    std::memcpy(h.magic, "VMTPOLY1", 8);
+    h.version = 1;
+    h.variant = variant;
+    h.deg = vmt::gf2::degree(mu);
+    h.nw = nw;
+    h.nlo = static_cast<int32_t>(lo.size());
+    h.nhi = static_cast<int32_t>(hi.size());
+    Poly m = mu;
+    m.resize(static_cast<size_t>(nw) + 1, 0);
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(m.data(), 8, m.size(), f) == m.size();
+    for (const auto& p : lo) ok = ok && std::fwrite(p.data(), 8, p.size(), f) == p.size();
+    for (const auto& p : hi) ok = ok && std::fwrite(p.data(), 8, p.size(), f) == p.size();
+    std::fclose(f);
+    if (ok) std::rename(tmp.c_str(), path.c_str());
+    else std::remove(tmp.c_str());
+}
+
+// Output bits of the variant's own generator, produced by the CUDA kernels
+// (seed 5489, one lane): the sequence Berlekamp-Massey works on.
+int sample_bits(int variant, int bit, int64_t nbits, std::vector<uint64_t>& packed, cudaStream_t st)
+{
+    const int n_units = vmt::units_per_lane(variant);
+    const int wb = vmt::word_bytes(variant);
+    const int64_t unit_bytes = static_cast<int64_t>(wb) * vmt::words_per_unit(variant);
+    // words needed: one bit per native word (MT) or per element (SFMT)
+    const int64_t words = (variant == VMT_SFMT19937) ? 4 * nbits : nbits;
+    unsigned long long* d_seed = nullptr;
+    void* d_state = nullptr;
+    void* d_out = nullptr;
+    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_seed), 8, st));
+    CUDA_TRY(cudaMallocAsync(&d_state, n_units * unit_bytes, st));
+    CUDA_TRY(cudaMallocAsync(&d_out, words * wb, st));
+    const unsigned long long seed = 5489ull;
+    CUDA_TRY(cudaMemcpyAsync(d_seed, &seed, 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(vmt::launch_seed(variant, 1, d_seed, d_state, st));
+    vmt::GenArgs a{};
+    a.states = d_state;
+    a.gens = 1;
+    a.gen0 = 0;
+    a.pos = static_cast<int>(vmt::block_words(variant, 1));
+    a.total = words;
+    a.nseg = 1;
+    a.seg[0].out = static_cast<char*>(d_out);
+    a.seg[0].count = words;
+    a.seg[0].wbeg = 0;
+    a.seg[0].wend = words;
+    a.seg[0].dtype = (variant == VMT_MT19937_64) ? VMT_U64 : VMT_U32;
+    a.seg[0].fast = 0;
+    CUDA_TRY(vmt::launch_generate(variant, 1, a, st));
+    std::vector<unsigned char> host(static_cast<size_t>(words * wb));
+    CUDA_TRY(cudaMemcpyAsync(host.data(), d_out, words * wb, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFreeAsync(d_seed, st);
+    cudaFreeAsync(d_state, st);
+    cudaFreeAsync(d_out, st);
+    packed.assign(static_cast<size_t>((nbits + 63) / 64), 0);
+    for (int64_t i = 0; i < nbits; ++i) {
+        uint64_t v;
+        if (variant == VMT_MT19937_64) std::memcpy(&v, &host[static_cast<size_t>(i) * 8], 8);
+        else {
+            uint32_t u;
+            const int64_t widx = (variant == VMT_SFMT19937) ? 4 * i + bit / 32 : i;
+            std::memcpy(&u, &host[static_cast<size_t>(widx) * 4], 4);
+            v = u;
+        }
+        const int b = (variant == VMT_SFMT19937) ? bit % 32 : bit;
+        if ((v >> b) & 1ull) packed[static_cast<size_t>(i >> 6)] |= 1ull << (i & 63);
+    }
+    return VMT_OK;
+}
+
+int ensure_variant(int variant, cudaStream_t st)
+{
+    VariantCtx& c = g_ctx[variant];
+    std::lock_guard<std::mutex> lk(c.mu_lock);
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (c.ready && c.device == dev) return VMT_OK;
+    if (!c.ready) {
+        Poly mu;
+        std::vector<Poly> lo, hi;
+        if (!load_cache(variant, mu, lo, hi)) {
+            const int64_t nbits = 2 * 19968 + 256;
+            std::vector<uint64_t> bits;
+            const int top = (variant == VMT_MT19937_32) ? 31 : (variant == VMT_MT19937_64 ? 63 : 0);
+            int rc = sample_bits(variant, top, nbits, bits, st);
+            if (rc) return rc;
+            mu = vmt::gf2::berlekamp_massey(bits.data(), nbits);
+            if (variant == VMT_SFMT19937) {
+                // the lcm over a few bit positions reaches the full minimal polynomial
+                const int extra[] = {32, 64, 96, 1, 33, 65, 97};
+                for (int b : extra) {
+                    if (vmt::gf2::degree(mu) >= 19968) break;
+                    rc = sample_bits(variant, b, nbits, bits, st);
+                    if (rc) return rc;
+                    Poly m2 = vmt::gf2::berlekamp_massey(bits.data(), nbits);
+                    Poly g = vmt::gf2::gcd(mu, m2);
+                    mu = vmt::gf2::mul_plain(mu, vmt::gf2::div_exact(m2, g));
+                }
+            }
+            const int D = vmt::gf2::degree(mu);
+            if ((variant != VMT_SFMT19937 && D != kPeriodExp) || (variant == VMT_SFMT19937 && D < kPeriodExp))
+                return fail(VMT_ECUDA, "minimal polynomial has unexpected degree " + std::to_string(D));
+            vmt::gf2::Modulus mod(mu);
+            lo.clear();
+            hi.clear();
+            Poly r = mod.x_pow_2q(0);
+            for (int q = 0; q <= kPeriodExp; ++q) {
+                if (q < kChainLo) lo.push_back(r);
+                if (q >= kChainHiFrom) hi.push_back(r);
+                if (q < kPeriodExp) r = mod.sqr(r);
+            }
+            if (variant != VMT_SFMT19937) {
+                // x^(2^p) = x mod mu for the primitive degree-p polynomial of MT
+                Poly x(2, 0);
+                x[0] = 2;
+                if (vmt::gf2::degree(mod.reduce(x)) != 1 ||
+                    !std::equal(hi.back().begin(), hi.back().end(), mod.reduce(x).begin()))
+                    return fail(VMT_ECUDA, "minimal polynomial failed the x^(2^19937) = x check");
+            }
+            save_cache(variant, mu, mod.words(), lo, hi);
+        }
+        c.mod.reset(new vmt::gf2::Modulus(mu));
+        c.chain_lo = std::move(lo);
+        c.chain_hi = std::move(hi);
+        // lane rows: x^(s * 2^19933), s = 0..15
+        c.lane_rows.assign(16, Poly());
+        Poly one(1, 1);
+        c.lane_rows[0] = c.mod->reduce(one);
+        const Poly& xJ = c.chain_hi[static_cast<size_t>(kLaneRowQ - kChainHiFrom)];
+        for (int s = 1; s < 16; ++s) c.lane_rows[static_cast<size_t>(s)] = c.mod->mul(c.lane_rows[static_cast<size_t>(s - 1)], xJ);
+        c.ready = true;
+        c.digits_ready = false;
+        c.device = -1;
+    }
+    if (c.device != dev) {
+        const size_t rows = 16 + kDigitRows;
+        if (c.d_table) cudaFree(c.d_table);
+        c.d_table = nullptr;
+        CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&c.d_table), rows * vmt::kPolyWords * sizeof(uint32_t)));
+        std::vector<uint32_t> host(16 * static_cast<size_t>(vmt::kPolyWords));
+        c.row_deg.assign(rows, -1);
+        for (int s = 0; s < 16; ++s) {
+            to_rows(c.lane_rows[static_cast<size_t>(s)], &host[static_cast<size_t>(s) * vmt::kPolyWords]);
+            c.row_deg[static_cast<size_t>(s)] = vmt::gf2::degree(c.lane_rows[static_cast<size_t>(s)]);
+        }
+        CUDA_TRY(cudaMemcpy(c.d_table, host.data(), host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        c.device = dev;
+        c.digits_ready = false;
+    }
+    return VMT_OK;
+}
+
+// base-256 digit rows for per-generator jump offsets d < 2^64
+int ensure_digits(int variant)
+{
+    VariantCtx& c = g_ctx[variant];
+    std::lock_guard<std::mutex> lk(c.mu_lock);
+    if (c.digits_ready) return VMT_OK;
+    std::vector<uint32_t> host(static_cast<size_t>(kDigitRows) * vmt::kPolyWords);
+    std::vector<Poly> rows(static_cast<size_t>(kDigitRows));
+    // x^(v 256^i) = (x^(256^i))^v; digit positions are independent -> threads
+    std::vector<std::thread> th;
+    for (int i = 0; i < 8; ++i)
+        th.emplace_back([&, i]() {
+            const Poly& base = c.chain_lo[static_cast<size_t>(8 * i)];
+            Poly cur = base;
+            for (int v = 1; v <= 255; ++v) {
+                if (v > 1) cur = c.mod->mul(cur, base);
+                rows[static_cast<size_t>(255 * i + v - 1)] = cur;
+            }
+        });
+    for (auto& t : th) t.join();
+    for (int r = 0; r < kDigitRows; ++r) {
+        to_rows(rows[static_cast<size_t>(r)], &host[static_cast<size_t>(r) * vmt::kPolyWords]);
+        c.row_deg[static_cast<size_t>(16 + r)] = vmt::gf2::degree(rows[static_cast<size_t>(r)]);
+    }
+    CUDA_TRY(cudaMemcpy(c.d_table + 16 * static_cast<size_t>(vmt::kPolyWords), host.data(),
+                        host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    c.digits_ready = true;
+    return VMT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// state object
+// ---------------------------------------------------------------------------
+struct vmt_state {
+    int variant = 0;
+    int lanes = 0;
+    int64_t count = 0;
+    int64_t block_pos = 0;     // native words of the current block already emitted
+    void* d_states = nullptr;  // [count][block words]
+    int device = 0;
+};
+
+namespace {
+
+int64_t state_total_bytes(const vmt_state* st) { return st->count * vmt::state_bytes_per_gen(st->variant, st->lanes); }
+
+int run_jump_items(int variant, const std::vector<vmt::JumpItem>& items, const uint32_t* table, cudaStream_t s)
+{
+    if (items.empty()) return VMT_OK;
+    vmt::JumpItem* d_items = nullptr;
+    const size_t bytes = items.size() * sizeof(vmt::JumpItem);
+    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_items), bytes, s));
+    CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), bytes, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(vmt::launch_jump(variant, d_items, static_cast<long long>(items.size()), table, s));
+    CUDA_TRY(cudaFreeAsync(d_items, s));
+    // the items vector is host memory read by the async copy: keep it alive
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return VMT_OK;
+}
+
+int64_t new_block_pos(int64_t B, int64_t p, int64_t total)
+{
+    if (total <= 0) return p;
+    int64_t first = (p < B) ? std::min(B - p, total) : 0;
+    int64_t rem = total - first;
+    if (rem == 0) return p + first;
+    const int64_t nblocks = (rem + B - 1) / B;
+    return rem - (nblocks - 1) * B;
+}
+
+int words_per_output(int variant, int dtype)
+{
+    if (variant == VMT_MT19937_64) return 1;
+    return (dtype == VMT_U64 || dtype == VMT_F64) ? 2 : 1;
+}
+
+int elem_bytes(int dtype) { return (dtype == VMT_U32 || dtype == VMT_F32) ? 4 : 8; }
+
+int vector_width(int variant, int lanes)
+{
+    if (variant == VMT_SFMT19937) return 4;
+    if (variant == VMT_MT19937_32) return std::min(lanes, 4);
+    return std::min(lanes, 2);
+}
+
+int generate_impl(vmt_state* st, int nseg, const int64_t* counts, const int* dtypes, void* const* outs,
+                  cudaStream_t s)
+{
+    if (!st) return fail(VMT_EINVAL, "null state");
+    if (nseg < 1 || nseg > VMT_MAXSEG) return fail(VMT_EINVAL, "nseg must be in 1..4");
+    const int v = st->variant;
+    vmt::GenArgs a{};
+    a.states = st->d_states;
+    a.gens = st->count;
+    a.gen0 = 0;
+    a.pos = static_cast<int>(st->block_pos);
+    a.nseg = nseg;
+    int64_t w = 0;
+    bool generic = false;
+    for (int i = 0; i < nseg; ++i) {
+        const int dt = dtypes[i];
+        if (dt < VMT_U32 || dt > VMT_F64) return fail(VMT_EINVAL, "bad dtype");
+        if (v == VMT_MT19937_64 && dt == VMT_U32) return fail(VMT_EINVAL, "u32 output is not defined for MT19937-64");
+        if (counts[i] < 0) return fail(VMT_EINVAL, "negative count");
+        if (counts[i] > 0 && !outs[i]) return fail(VMT_EINVAL, "null output pointer");
+        const int wpo = words_per_output(v, dt);
+        vmt::SegArg& sg = a.seg[i];
+        sg.out = static_cast<char*>(outs[i]);
+        sg.count = counts[i];
+        sg.wbeg = w;
+        sg.wend = w + counts[i] * wpo;
+        sg.dtype = dt;
+        const int eb = elem_bytes(dt);
+        sg.fast = ((reinterpret_cast<uintptr_t>(outs[i]) & 15u) == 0 && ((counts[i] * eb) % 16) == 0) ? 1 : 0;
+        if (wpo == 2 && counts[i] > 0) {
+            // a pair must sit inside one thread's vector: even absolute start and
+            // vectors of at least two words
+            if (((st->block_pos + w) & 1) != 0 || vector_width(v, st->lanes) < 2) generic = true;
+        }
+        w += counts[i] * wpo;
+    }
+    a.total = w;
+    if (w == 0) return VMT_OK;
+    const int64_t B = vmt::block_words(v, st->lanes);
+    if (!generic) {
+        CUDA_TRY(vmt::launch_generate(v, st->lanes, a, s));
+    } else {
+        // raw native words into scratch, then one conversion per segment
+        const int wb = vmt::word_bytes(v);
+        void* scratch = nullptr;
+        CUDA_TRY(cudaMallocAsync(&scratch, static_cast<size_t>(st->count * w * wb), s));
+        vmt::GenArgs r = a;
+        r.nseg = 1;
+        r.seg[0].out = static_cast<char*>(scratch);
+        r.seg[0].count = w;
+        r.seg[0].wbeg = 0;
+        r.seg[0].wend = w;
+        r.seg[0].dtype = (v == VMT_MT19937_64) ? VMT_U64 : VMT_U32;
+        r.seg[0].fast = 0;
+        CUDA_TRY(vmt::launch_generate(v, st->lanes, r, s));
+        for (int i = 0; i < nseg; ++i)
+            CUDA_TRY(vmt::launch_convert(scratch, w, v == VMT_MT19937_64, st->count, a.seg[i].wbeg, a.seg[i].dtype,
+                                         a.seg[i].count, a.seg[i].out, s));
+        CUDA_TRY(cudaFreeAsync(scratch, s));
+    }
+    st->block_pos = new_block_pos(B, st->block_pos, w);
+    return VMT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* vmt_last_error(void) { return g_err.c_str(); }
+
+int vmt_set_cache_dir(const char* path)
+{
+    std::lock_guard<std::mutex> lk(g_cache_lock);
+    g_cache_dir = path ? std::string(path) : std::string();
+    return VMT_OK;
+}
+
+int vmt_init_batch(vmt_state** out, int variant, int lanes, int64_t count, const uint64_t* seeds,
+                   const uint64_t* jumps, void* cuda_stream)
+{
+    if (!out) return fail(VMT_EINVAL, "null output handle");
+    *out = nullptr;
+    if (!valid_variant(variant)) return fail(VMT_EINVAL, "bad variant");
+    if (!valid_lanes(lanes)) return fail(VMT_EINVAL, "lanes must be 1, 2, 4, 8 or 16");
+    if (count < 1 || !seeds) return fail(VMT_EINVAL, "count must be >= 1 and seeds non-null");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int rc = ensure_variant(variant, s);
+    if (rc) return rc;
+    bool any_jump = false;
+    if (jumps)
+        for (int64_t g = 0; g < count && !any_jump; ++g) any_jump = jumps[g] != 0;
+    if (any_jump && (rc = ensure_digits(variant))) return rc;
+    VariantCtx& c = g_ctx[variant];
+
+    std::unique_ptr<vmt_state> st(new vmt_state());
+    st->variant = variant;
+    st->lanes = lanes;
+    st->count = count;
+    CUDA_TRY(cudaGetDevice(&st->device));
+    const int64_t bytes = state_total_bytes(st.get());
+    if (cudaMalloc(&st->d_states, static_cast<size_t>(bytes)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VMT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " state bytes failed");
+    }
+    const int n_units = vmt::units_per_lane(variant);
+    const int64_t unit_bytes = static_cast<int64_t>(vmt::word_bytes(variant)) * vmt::words_per_unit(variant);
+    // scratch: seeds and the unjumped base states, unit-major [u][g]
+    unsigned long long* d_seeds = nullptr;
+    char* d_base = nullptr;
+    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_seeds), static_cast<size_t>(count) * 8, s));
+    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_base), static_cast<size_t>(count * n_units * unit_bytes), s));
+    CUDA_TRY(cudaMemcpyAsync(d_seeds, seeds, static_cast<size_t>(count) * 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(vmt::launch_seed(variant, count, d_seeds, d_base, s));
+    if (any_jump) {
+        // base <- x^(d)(F) base, one base-256 digit per launch (jumps commute)
+        for (int i = 0; i < 8; ++i) {
+            std::vector<vmt::JumpItem> items;
+            for (int64_t g = 0; g < count; ++g) {
+                const int dig = static_cast<int>((jumps[g] >> (8 * i)) & 255u);
+                if (!dig) continue;
+                vmt::JumpItem it{};
+                it.src = d_base + g * unit_bytes;
+                it.dst = d_base + g * unit_bytes;
+                it.src_stride = static_cast<int>(count);
+                it.dst_stride = static_cast<int>(count);
+                it.poly = 16 + 255 * i + dig - 1;
+                it.deg = c.row_deg[static_cast<size_t>(it.poly)];
+                items.push_back(it);
+            }
+            if ((rc = run_jump_items(variant, items, c.d_table, s))) return rc;
+        }
+    }
+    // lane fan-out: lane t = x^(t J)(F) base, written into X-hat's column t
+    {
+        std::vector<vmt::JumpItem> items;
+        items.reserve(static_cast<size_t>(count * lanes));
+        const int64_t gen_bytes = vmt::state_bytes_per_gen(variant, lanes);
+        for (int64_t g = 0; g < count; ++g)
+            for (int t = 0; t < lanes; ++t) {
+                vmt::JumpItem it{};
+                it.src = d_base + g * unit_bytes;
+                it.src_stride = static_cast<int>(count);
+                it.dst = static_cast<char*>(st->d_states) + g * gen_bytes + t * unit_bytes;
+                it.dst_stride = lanes;
+                it.poly = t * 16 / lanes;
+                it.deg = c.row_deg[static_cast<size_t>(it.poly)];
+                items.push_back(it);
+            }
+        if ((rc = run_jump_items(variant, items, c.d_table, s))) return rc;
+    }
+    CUDA_TRY(cudaFreeAsync(d_seeds, s));
+    CUDA_TRY(cudaFreeAsync(d_base, s));
+    st->block_pos = vmt::block_words(variant, lanes);  // exhausted: the first output twists
+    *out = st.release();
+    return VMT_OK;
+}
+
+int vmt_init(vmt_state** st, int variant, int lanes, uint64_t seed, uint64_t jump, void* cuda_stream)
+{
+    return vmt_init_batch(st, variant, lanes, 1, &seed, &jump, cuda_stream);
+}
+
+int vmt_jump(vmt_state* st, const uint64_t* poly, int64_t nbits, void* cuda_stream)
+{
+    if (!st || !poly) return fail(VMT_EINVAL, "null argument");
+    if (nbits < 0 || nbits > 32 * vmt::kPolyWords - 64) return fail(VMT_EINVAL, "nbits out of range");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<uint32_t> row(static_cast<size_t>(vmt::kPolyWords), 0);
+    const int64_t nw = (nbits + 63) / 64;
+    Poly p(poly, poly + nw);
+    if (nbits % 64 && nw) p[static_cast<size_t>(nw - 1)] &= (1ull << (nbits % 64)) - 1;
+    to_rows(p, row.data());
+    const int deg = vmt::gf2::degree(p);
+    uint32_t* d_row = nullptr;
+    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_row), row.size() * 4, s));
+    CUDA_TRY(cudaMemcpyAsync(d_row, row.data(), row.size() * 4, cudaMemcpyHostToDevice, s));
+    std::vector<vmt::JumpItem> items;
+    const int64_t unit_bytes = static_cast<int64_t>(vmt::word_bytes(st->variant)) * vmt::words_per_unit(st->variant);
+    const int64_t gen_bytes = vmt::state_bytes_per_gen(st->variant, st->lanes);
+    for (int64_t g = 0; g < st->count; ++g)
+        for (int t = 0; t < st->lanes; ++t) {
+            vmt::JumpItem it{};
+            it.src = static_cast<char*>(st->d_states) + g * gen_bytes + t * unit_bytes;
+            it.dst = const_cast<void*>(it.src);
+            it.src_stride = st->lanes;
+            it.dst_stride = st->lanes;
+            it.poly = 0;
+            it.deg = deg;
+            items.push_back(it);
+        }
+    int rc = run_jump_items(st->variant, items, d_row, s);
+    cudaFreeAsync(d_row, s);
+    return rc;
+}
+
+int vmt_jump_poly(int variant, uint64_t d, int log2_extra, uint64_t* poly_out, int64_t cap_words)
+{
+    if (!valid_variant(variant) || !poly_out || log2_extra < 0) return fail(VMT_EINVAL, "bad argument");
+    int rc = ensure_variant(variant, nullptr);
+    if (rc) return rc;
+    VariantCtx& c = g_ctx[variant];
+    // x^(d 2^e) = (x^d)^(2^e): e squarings of x^d, using the stored chain for x^(2^q)
+    Poly r;
+    {
+        Poly one(1, 1);
+        r = c.mod->reduce(one);
+        for (int q = 0; q < 64; ++q)
+            if ((d >> q) & 1ull) r = c.mod->mul(r, c.chain_lo[static_cast<size_t>(q)]);
+    }
+    for (int i = 0; i < log2_extra; ++i) r = c.mod->sqr(r);
+    const int64_t nw = static_cast<int64_t>(r.size());
+    if (cap_words < nw) return fail(VMT_EINVAL, "poly_out too small");
+    std::memset(poly_out, 0, static_cast<size_t>(cap_words) * 8);
+    std::memcpy(poly_out, r.data(), static_cast<size_t>(nw) * 8);
+    return static_cast<int>(nw);
+}
+
+int vmt_generate_multi(vmt_state* st, int nseg, const int64_t* counts, const int* dtypes, void* const* outs,
+                       void* cuda_stream)
+{
+    if (!counts || !dtypes || !outs) return fail(VMT_EINVAL, "null segment arrays");
+    return generate_impl(st, nseg, counts, dtypes, outs, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int vmt_generate(vmt_state* st, int64_t n, int dtype, void* out_dev, void* cuda_stream)
+{
+    void* outs[1] = {out_dev};
+    return generate_impl(st, 1, &n, &dtype, outs, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int vmt_generate_host(vmt_state* st, int64_t n, int dtype, void* out_host, void* cuda_stream)
+{
+    if (!st || (!out_host && n > 0)) return fail(VMT_EINVAL, "null argument");
+    if (n < 0) return fail(VMT_EINVAL, "negative count");
+    if (n == 0) return VMT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int eb = elem_bytes(dtype);
+    // chunk so that one staging buffer holds <= 256 MiB; two buffers alternate
+    int64_t chunk = std::max<int64_t>(1, (int64_t(256) << 20) / (eb * st->count));
+    chunk = std::min(chunk, n);
+    if (chunk > 4) chunk &= ~int64_t(3);
+    void* stage[2] = {nullptr, nullptr};
+    cudaStream_t cs = nullptr;
+    cudaEvent_t done_gen[2], done_copy[2];
+    CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+        CUDA_TRY(cudaMalloc(&stage[i], static_cast<size_t>(chunk * st->count * eb)));
+        CUDA_TRY(cudaEventCreateWithFlags(&done_gen[i], cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&done_copy[i], cudaEventDisableTiming));
+        CUDA_TRY(cudaEventRecord(done_copy[i], cs));
+    }
+    int rc = VMT_OK;
+    int64_t off = 0;
+    for (int k = 0; off < n && rc == VMT_OK; ++k) {
+        const int b = k & 1;
+        const int64_t m = std::min(chunk, n - off);
+        CUDA_TRY(cudaStreamWaitEvent(s, done_copy[b], 0));
+        rc = vmt_generate(st, m, dtype, stage[b], s);
+        if (rc) break;
+        CUDA_TRY(cudaEventRecord(done_gen[b], s));
+        CUDA_TRY(cudaStreamWaitEvent(cs, done_gen[b], 0));
+        CUDA_TRY(cudaMemcpy2DAsync(static_cast<char*>(out_host) + off * eb, static_cast<size_t>(n * eb), stage[b],
+                                   static_cast<size_t>(m * eb), static_cast<size_t>(m * eb),
+                                   static_cast<size_t>(st->count), cudaMemcpyDeviceToHost, cs));
+        CUDA_TRY(cudaEventRecord(done_copy[b], cs));
+        off += m;
+    }
+    CUDA_TRY(cudaStreamSynchronize(cs));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(stage[i]);
+        cudaEventDestroy(done_gen[i]);
+        cudaEventDestroy(done_copy[i]);
+    }
+    cudaStreamDestroy(cs);
+    return rc;
+}
+
+struct ExportHeader {
+    char magic[8];
+    int32_t version, variant, lanes, pad;
+    int64_t count, block_pos, state_bytes;
+};
+
+int64_t vmt_state_bytes(const vmt_state* st)
+{
+    if (!st) return fail(VMT_EINVAL, "null state");
+    return static_cast<int64_t>(sizeof(ExportHeader)) + state_total_bytes(st);
+}
+
+int vmt_state_export(const vmt_state* st, void* host_buf, size_t cap, void* cuda_stream)
+{
+    if (!st || !host_buf) return fail(VMT_EINVAL, "null argument");
+    const int64_t need = vmt_state_bytes(st);
+    if (static_cast<int64_t>(cap) < need) return fail(VMT_EINVAL, "buffer too small");
+    ExportHeader h{};
+    std::memcpy(h.magic, "VMTSTAT1", 8);
+    h.version = 1;
+    h.variant = st->variant;
+    h.lanes = st->lanes;
+    h.count = st->count;
+    h.block_pos = st->block_pos;
+    h.state_bytes = state_total_bytes(st);
+    std::memcpy(host_buf, &h, sizeof(h));
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(host_buf) + sizeof(h), st->d_states, static_cast<size_t>(h.state_bytes),
+                             cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return VMT_OK;
+}
+
+int vmt_state_import(vmt_state* st, const void* host_buf, size_t len, void* cuda_stream)
+{
+    if (!st || !host_buf) return fail(VMT_EINVAL, "null argument");
+    if (len < sizeof(ExportHeader)) return fail(VMT_ESTATE, "buffer shorter than the header");
+    ExportHeader h{};
+    std::memcpy(&h, host_buf, sizeof(h));
+    if (std::memcmp(h.magic, "VMTSTAT1", 8) != 0 || h.version != 1) return fail(VMT_ESTATE, "not a vmt state export");
+    if (h.variant != st->variant || h.lanes != st->lanes || h.count != st->count ||
+        h.state_bytes != state_total_bytes(st))
+        return fail(VMT_ESTATE, "export does not match this state object");
+    if (static_cast<int64_t>(len) < static_cast<int64_t>(sizeof(h)) + h.state_bytes)
+        return fail(VMT_ESTATE, "truncated export");
+    const int64_t B = vmt::block_words(st->variant, st->lanes);
+    if (h.block_pos < 0 || h.block_pos > B) return fail(VMT_ESTATE, "block position out of range");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    CUDA_TRY(cudaMemcpyAsync(st->d_states, static_cast<const char*>(host_buf) + sizeof(h),
+                             static_cast<size_t>(h.state_bytes), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    st->block_pos = h.block_pos;
+    return VMT_OK;
+}
+
+int vmt_state_info(const vmt_state* st, int* variant, int* lanes, int64_t* count, int64_t* block_pos)
+{
+    if (!st) return fail(VMT_EINVAL, "null state");
+    if (variant) *variant = st->variant;
+    if (lanes) *lanes = st->lanes;
+    if (count) *count = st->count;
+    if (block_pos) *block_pos = st->block_pos;
+    return VMT_OK;
+}
+
+void* vmt_state_device_ptr(const vmt_state* st) { return st ? st->d_states : nullptr; }
+
+void vmt_free(vmt_state* st)
+{
+    if (!st) return;
+    if (st->d_states) cudaFree(st->d_states);
+    delete st;
+}
+
+int vmt_poly_minpoly(const uint64_t* bits, int64_t n, uint64_t* mu_out, int64_t cap_words)
+{
+    if (!bits || !mu_out || n < 1) return fail(VMT_EINVAL, "bad argument");
+    Poly mu = vmt::gf2::berlekamp_massey(bits, n);
+    const int d = vmt::gf2::degree(mu);
+    const int64_t nw = d / 64 + 1;
+    if (cap_words < nw) return fail(VMT_EINVAL, "mu_out too small");
+    std::memset(mu_out, 0, static_cast<size_t>(cap_words) * 8);
+    std::memcpy(mu_out, mu.data(), static_cast<size_t>(nw) * 8);
+    return d;
+}
+
+int vmt_poly_mulmod(const uint64_t* a, const uint64_t* b, const uint64_t* mu, uint64_t* out, int64_t nw)
+{
+    if (!a || !b || !mu || !out || nw < 1) return fail(VMT_EINVAL, "bad argument");
+    try {
+        vmt::gf2::Modulus m(Poly(mu, mu + nw));
+        Poly r = m.mul(Poly(a, a + nw), Poly(b, b + nw));
+        std::memset(out, 0, static_cast<size_t>(nw) * 8);
+        std::memcpy(out, r.data(), std::min<size_t>(r.size(), static_cast<size_t>(nw)) * 8);
+    } catch (const std::exception& e) {
+        return fail(VMT_EINVAL, e.what());
+    }
+    return VMT_OK;
+}
+
+int vmt_poly_x2pow(const uint64_t* mu, int64_t nw, int q_lo, int q_hi, uint64_t* out)
+{
+    if (!mu || !out || nw < 1 || q_lo < 0 || q_hi < q_lo) return fail(VMT_EINVAL, "bad argument");
+    try {
+        vmt::gf2::Modulus m(Poly(mu, mu + nw));
+        Poly r = m.x_pow_2q(0);
+        for (int q = 0; q <= q_hi; ++q) {
+            if (q >= q_lo) {
+                uint64_t* dst = out + static_cast<int64_t>(q - q_lo) * nw;
+                std::memset(dst, 0, static_cast<size_t>(nw) * 8);
+                std::memcpy(dst, r.data(), std::min<size_t>(r.size(), static_cast<size_t>(nw)) * 8);
+            }
+            if (q < q_hi) r = m.sqr(r);
+        }
+    } catch (const std::exception& e) {
+        return fail(VMT_EINVAL, e.what());
+    }
+    return VMT_OK;
+}
+
+}  // extern "C"

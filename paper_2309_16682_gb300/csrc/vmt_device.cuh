@@ -1,0 +1,260 @@
+// vmt_device.cuh -- device-side building blocks shared by the V-family kernels.
+//
+// Generators (arXiv 2309.16682):
+//   MT19937-32  Sec. 2.2 eq. (params):   (w,n,m,r) = (32,624,397,31), a = 9908B0DF
+//   MT19937-64  Sec. 2.3 eq. (params64): (64,312,156,31), a = B5026F5AA96619E9
+//   SFMT19937   Sec. 2.4 eq. (sfmt_params): (128,156,122), K = (DFFFFFEF, DDFECB7F,
+//               BFFAFFFF, BFFFFFF6)
+// Recurrence eq. (step) with the multiplication by A of eq. (matmult), the
+// tempering eq. (tempering) and the SFMT recurrence eq. (sfmt_step).
+//
+// Output conversions are not in the paper; their definitions:
+//   f32 from a 32-bit word z:  (z >> 8) * 2^-24           (exact)
+//   f32 from a 64-bit word z:  (z >> 40) * 2^-24          (exact)
+//   f64 from a 64-bit word z:  (z >> 11) * 2^-53          (exact)
+//   f64 from two 32-bit words (a, b):  ((a >> 5) 2^26 + (b >> 6)) 2^-53
+//   u64 from two 32-bit words (a, b):  a | b << 32
+// The f64 value is assembled from integer fields (no FP64 instruction): the
+// 53-bit integer v is normalised with a leading-zero count and its exponent
+// written directly, which is exact because v < 2^53.
+#pragma once
+#include <cstdint>
+
+#include "vmt_internal.hpp"
+
+namespace vmt {
+namespace dev {
+
+// ----------------------------------------------------------------------------
+// generator constants
+// ----------------------------------------------------------------------------
+struct MT32 {
+    using W = uint32_t;
+    static constexpr int N = 624, MM = 397;
+    static __device__ __forceinline__ W twist(W xk, W xk1, W xkm)
+    {
+        const W y = (xk & 0x80000000u) | (xk1 & 0x7FFFFFFFu);
+        // y * A: y >> 1, XOR a when y is odd; y's lowest bit is xk1's lowest bit
+        return xkm ^ (y >> 1) ^ ((xk1 & 1u) * 0x9908B0DFu);
+    }
+    static __device__ __forceinline__ W temper(W y)
+    {
+        y ^= y >> 11;
+        y ^= (y << 7) & 0x9D2C5680u;
+        y ^= (y << 15) & 0xEFC60000u;
+        return y ^ (y >> 18);
+    }
+};
+
+struct MT64 {
+    using W = unsigned long long;
+    static constexpr int N = 312, MM = 156;
+    static __device__ __forceinline__ W twist(W xk, W xk1, W xkm)
+    {
+        const W y = (xk & 0xFFFFFFFF80000000ull) | (xk1 & 0x7FFFFFFFull);
+        return xkm ^ (y >> 1) ^ ((xk1 & 1ull) * 0xB5026F5AA96619E9ull);
+    }
+    static __device__ __forceinline__ W temper(W y)
+    {
+        y ^= (y >> 29) & 0x5555555555555555ull;
+        y ^= (y << 17) & 0x71D67FFFEDA60000ull;
+        y ^= (y << 37) & 0xFFF7EEE000000000ull;
+        return y ^ (y >> 43);
+    }
+};
+
+__device__ __constant__ static const uint32_t kSfmtMask[4] = {0xDFFFFFEFu, 0xDDFECB7Fu, 0xBFFAFFFFu, 0xBFFFFFF6u};
+
+// ----------------------------------------------------------------------------
+// conversions
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float f32_of_u32(uint32_t z) { return __uint2float_rz(z >> 8) * 5.9604644775390625e-8f; }
+
+// exact double of v * 2^-53 for 0 <= v < 2^53, built from integer fields
+__device__ __forceinline__ double f64_of_53(unsigned long long v)
+{
+    if (v == 0ull) return 0.0;
+    const int sh = __clzll(v) - 11;  // leading one moved to bit 52
+    const unsigned long long bits = (v << sh) + (static_cast<unsigned long long>(1021 - sh) << 52);
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+
+__device__ __forceinline__ double f64_of_u64(unsigned long long z) { return f64_of_53(z >> 11); }
+__device__ __forceinline__ double f64_of_pair(uint32_t a, uint32_t b)
+{
+    return f64_of_53((static_cast<unsigned long long>(a >> 5) << 26) | (b >> 6));
+}
+__device__ __forceinline__ float f32_of_u64(unsigned long long z) { return f32_of_u32(static_cast<uint32_t>(z >> 32)); }
+
+// ----------------------------------------------------------------------------
+// Emitter: routes word e (call-relative index in the V-stream) of generator g
+// to its segment, converts it and stores it.
+// ----------------------------------------------------------------------------
+struct Emitter {
+    const GenArgs& a;
+    long long g;  // generator index within the output arrays
+
+    __device__ __forceinline__ int seg_of(long long e) const
+    {
+        int s = 0;
+#pragma unroll
+        for (int i = 1; i < VMT_MAXSEG; ++i)
+            if (i < a.nseg && e >= a.seg[i].wbeg) s = i;
+        return s;
+    }
+
+    // 32-bit words: z[0..VW) are words f0..f0+VW-1 of the block; the valid
+    // block range is [lo, hi) and word f maps to e = ebase + f - lo.
+    template <int VW>
+    __device__ __forceinline__ void emit32(long long f0, const uint32_t (&z)[VW], long long lo, long long hi,
+                                           long long ebase) const
+    {
+        const long long e0 = ebase + f0 - lo;
+        if (f0 >= lo && f0 + VW <= hi) {
+            const int s = seg_of(e0);
+            const SegArg& sg = a.seg[s];
+            const long long rel = e0 - sg.wbeg;
+            if (sg.fast && e0 + VW <= sg.wend && (rel % VW) == 0) {
+                store_vec32<VW>(sg, rel, z);
+                return;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+            const long long f = f0 + u;
+            if (f < lo || f >= hi) continue;
+            const long long e = e0 + u;
+            const SegArg& sg = a.seg[seg_of(e)];
+            const long long rel = e - sg.wbeg;
+            char* base = sg.out;
+            const long long idx = g * sg.count;
+            switch (sg.dtype) {
+            case VMT_U32: reinterpret_cast<uint32_t*>(base)[idx + rel] = z[u]; break;
+            case VMT_F32: reinterpret_cast<float*>(base)[idx + rel] = f32_of_u32(z[u]); break;
+            case VMT_U64:
+                if ((rel & 1) == 0 && u + 1 < VW)
+                    reinterpret_cast<unsigned long long*>(base)[idx + rel / 2] =
+                        static_cast<unsigned long long>(z[u]) | (static_cast<unsigned long long>(z[u + 1]) << 32);
+                break;
+            case VMT_F64:
+                if ((rel & 1) == 0 && u + 1 < VW)
+                    reinterpret_cast<double*>(base)[idx + rel / 2] = f64_of_pair(z[u], z[u + 1]);
+                break;
+            }
+        }
+    }
+
+    template <int VW>
+    __device__ __forceinline__ void store_vec32(const SegArg& sg, long long rel, const uint32_t (&z)[VW]) const
+    {
+        char* base = sg.out;
+        const long long idx = g * sg.count;
+        if (VW == 4) {
+            switch (sg.dtype) {
+            case VMT_U32:
+                __stcs(reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(base) + idx + rel),
+                       make_uint4(z[0], z[1 % VW], z[2 % VW], z[3 % VW]));
+                break;
+            case VMT_F32:
+                __stcs(reinterpret_cast<float4*>(reinterpret_cast<float*>(base) + idx + rel),
+                       make_float4(f32_of_u32(z[0]), f32_of_u32(z[1 % VW]), f32_of_u32(z[2 % VW]),
+                                   f32_of_u32(z[3 % VW])));
+                break;
+            case VMT_U64: {
+                ulonglong2 v;
+                v.x = static_cast<unsigned long long>(z[0]) | (static_cast<unsigned long long>(z[1 % VW]) << 32);
+                v.y = static_cast<unsigned long long>(z[2 % VW]) | (static_cast<unsigned long long>(z[3 % VW]) << 32);
+                __stcs(reinterpret_cast<ulonglong2*>(reinterpret_cast<unsigned long long*>(base) + idx + rel / 2), v);
+                break;
+            }
+            case VMT_F64: {
+                double2 v;
+                v.x = f64_of_pair(z[0], z[1 % VW]);
+                v.y = f64_of_pair(z[2 % VW], z[3 % VW]);
+                __stcs(reinterpret_cast<double2*>(reinterpret_cast<double*>(base) + idx + rel / 2), v);
+                break;
+            }
+            }
+        } else if (VW == 2) {
+            switch (sg.dtype) {
+            case VMT_U32:
+                __stcs(reinterpret_cast<uint2*>(reinterpret_cast<uint32_t*>(base) + idx + rel), make_uint2(z[0], z[1 % VW]));
+                break;
+            case VMT_F32:
+                __stcs(reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + idx + rel),
+                       make_float2(f32_of_u32(z[0]), f32_of_u32(z[1 % VW])));
+                break;
+            case VMT_U64:
+                __stcs(reinterpret_cast<unsigned long long*>(base) + idx + rel / 2,
+                       static_cast<unsigned long long>(z[0]) | (static_cast<unsigned long long>(z[1 % VW]) << 32));
+                break;
+            case VMT_F64:
+                __stcs(reinterpret_cast<double*>(base) + idx + rel / 2, f64_of_pair(z[0], z[1 % VW]));
+                break;
+            }
+        } else {
+            switch (sg.dtype) {
+            case VMT_U32: __stcs(reinterpret_cast<uint32_t*>(base) + idx + rel, z[0]); break;
+            case VMT_F32: __stcs(reinterpret_cast<float*>(base) + idx + rel, f32_of_u32(z[0])); break;
+            default: break;  // pairs never take the one-word vector path
+            }
+        }
+    }
+
+    // 64-bit words (MT19937-64): u64, f64 or f32 per word.
+    template <int VW>
+    __device__ __forceinline__ void emit64(long long f0, const unsigned long long (&z)[VW], long long lo,
+                                           long long hi, long long ebase) const
+    {
+        const long long e0 = ebase + f0 - lo;
+        if (f0 >= lo && f0 + VW <= hi) {
+            const int s = seg_of(e0);
+            const SegArg& sg = a.seg[s];
+            const long long rel = e0 - sg.wbeg;
+            if (sg.fast && e0 + VW <= sg.wend && (rel % VW) == 0) {
+                char* base = sg.out;
+                const long long idx = g * sg.count + rel;
+                if (VW == 2) {
+                    switch (sg.dtype) {
+                    case VMT_U64: {
+                        ulonglong2 v;
+                        v.x = z[0];
+                        v.y = z[1 % VW];
+                        __stcs(reinterpret_cast<ulonglong2*>(reinterpret_cast<unsigned long long*>(base) + idx), v);
+                        return;
+                    }
+                    case VMT_F64: {
+                        double2 v;
+                        v.x = f64_of_u64(z[0]);
+                        v.y = f64_of_u64(z[1 % VW]);
+                        __stcs(reinterpret_cast<double2*>(reinterpret_cast<double*>(base) + idx), v);
+                        return;
+                    }
+                    case VMT_F32:
+                        __stcs(reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + idx),
+                               make_float2(f32_of_u64(z[0]), f32_of_u64(z[1 % VW])));
+                        return;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+            const long long f = f0 + u;
+            if (f < lo || f >= hi) continue;
+            const long long e = e0 + u;
+            const SegArg& sg = a.seg[seg_of(e)];
+            const long long idx = g * sg.count + (e - sg.wbeg);
+            char* base = sg.out;
+            switch (sg.dtype) {
+            case VMT_U64: reinterpret_cast<unsigned long long*>(base)[idx] = z[u]; break;
+            case VMT_F64: reinterpret_cast<double*>(base)[idx] = f64_of_u64(z[u]); break;
+            case VMT_F32: reinterpret_cast<float*>(base)[idx] = f32_of_u64(z[u]); break;
+            default: break;
+            }
+        }
+    }
+};
+
+}  // namespace dev
+}  // namespace vmt

@@ -1,0 +1,62 @@
+// vmt_internal.hpp -- launch descriptors shared by the C-ABI layer and the
+// CUDA kernels.  Not part of the public interface (include/vmt.h is).
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/vmt.h"
+
+#define VMT_MAXSEG 4
+
+namespace vmt {
+
+// Block sizes in native words (u32 for MT19937-32 and SFMT19937, u64 for
+// MT19937-64): n * M * (u32 per unit).
+inline int units_per_lane(int variant) { return variant == VMT_MT19937_32 ? 624 : (variant == VMT_MT19937_64 ? 312 : 156); }
+inline int words_per_unit(int variant) { return variant == VMT_SFMT19937 ? 4 : 1; }
+inline int word_bytes(int variant) { return variant == VMT_MT19937_64 ? 8 : 4; }
+inline int64_t block_words(int variant, int lanes) { return static_cast<int64_t>(units_per_lane(variant)) * lanes * words_per_unit(variant); }
+inline int64_t state_bytes_per_gen(int variant, int lanes) { return block_words(variant, lanes) * word_bytes(variant); }
+
+// One output segment of a generate call.  Generator g writes its outputs of
+// this segment at out + g*count elements; the segment covers call-relative
+// native words [wbeg, wend).
+struct SegArg {
+    char* out;
+    long long count;
+    long long wbeg, wend;
+    int dtype;
+    int fast;  // out and count*elem_size are multiples of 16 bytes
+};
+
+struct GenArgs {
+    void* states;      // [gens][block words]
+    long long gens;    // generators in the launch
+    long long gen0;    // first generator's index in the output arrays
+    int pos;           // block position (native words) at call start, same for all
+    long long total;   // native words per generator in this call
+    int nseg;
+    SegArg seg[VMT_MAXSEG];
+};
+
+// Jump work item: dst = c(F) src for one lane-state.  Unit u of the source
+// state lives at src + u*src_stride units (a unit is one word, or one 128-bit
+// element for SFMT19937); likewise for dst.  src and dst may alias.
+struct JumpItem {
+    const void* src;
+    void* dst;
+    int src_stride;
+    int dst_stride;
+    int poly;      // row of the polynomial table
+    int deg;       // degree of that polynomial (-1: zero polynomial)
+};
+
+constexpr int kPolyWords = 640;  // u32 words per polynomial row (20480 bits)
+
+cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, cudaStream_t s);
+cudaError_t launch_seed(int variant, long long count, const unsigned long long* seeds, void* base, cudaStream_t s);
+cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s);
+cudaError_t launch_copy_lane(int variant, int lanes, long long gens, const void* base, void* states, cudaStream_t s);
+
+}  // namespace vmt

@@ -1,0 +1,94 @@
+"""CPU checks of the C-ABI library (no GPU needed).
+
+* libvmt.so loads and exports every function declared in include/vmt.h.
+* The library's host polynomial code (Berlekamp-Massey, products modulo mu, the
+  squaring chain) agrees with the oracle's independent implementation.  The
+  two share no code; agreement on the same inputs checks both.
+* Argument errors are reported with VMT_EINVAL before any device work.
+"""
+import ctypes
+import os
+import re
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import ROOT
+
+vmt = pytest.importorskip("paper_2309_16682_gb300")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2309_16682_gb300 import build
+    build.build()
+    return vmt.lib()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "vmt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vmt_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_all_declared_symbols_exported(L):
+    names = _declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_invalid_arguments_rejected(L):
+    h = ctypes.c_void_p()
+    seeds = np.array([1], np.uint64)
+    assert L.vmt_init_batch(ctypes.byref(h), 7, 4, 1, seeds.ctypes.data, None, None) == vmt.VMT_EINVAL
+    assert L.vmt_init_batch(ctypes.byref(h), 0, 3, 1, seeds.ctypes.data, None, None) == vmt.VMT_EINVAL
+    assert L.vmt_init_batch(ctypes.byref(h), 0, 4, 0, seeds.ctypes.data, None, None) == vmt.VMT_EINVAL
+    assert b"lanes" in L.vmt_last_error() or b"count" in L.vmt_last_error()
+    assert L.vmt_generate(None, 10, 0, None, None) == vmt.VMT_EINVAL
+    assert L.vmt_state_import(None, None, 0, None) == vmt.VMT_EINVAL
+
+
+@pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])
+def test_library_bm_matches_oracle_minpoly(L, oracle_polys, variant):
+    bits = O._bit_sequence(variant, 31 if variant == O.MT32 else (63 if variant == O.MT64 else 0), O._BM_LEN)
+    d, mu = vmt.poly_minpoly(bits)
+    ref = O.minpoly(variant)
+    assert d == O.poly_deg(ref)
+    n = min(mu.size, ref.size)
+    assert np.array_equal(mu[:n], ref[:n]) and not mu[n:].any() and not ref[n:].any()
+
+
+def test_library_mulmod_matches_oracle(L, oracle_polys):
+    rng = np.random.default_rng(4)
+    for variant in (O.MT32, O.SFMT):
+        mu = O.minpoly(variant)
+        nw = O.poly_deg(mu) // 64 + 1
+        for _ in range(3):
+            a = rng.integers(0, 2**63, size=O.NW, dtype=np.uint64)
+            b = rng.integers(0, 2**63, size=O.NW, dtype=np.uint64)
+            a[nw - 1:] = 0
+            b[nw - 1:] = 0
+            ref = O.poly_mulmod(a, b, mu)
+            got = vmt.poly_mulmod(a[:nw + 1], b[:nw + 1], mu[:nw + 1])
+            assert np.array_equal(got, ref[:nw + 1])
+
+
+def test_library_chain_matches_oracle(L, oracle_polys):
+    mu = O.minpoly(O.MT32)
+    nw = 313
+    got = vmt.poly_x2pow(mu[:nw], 0, 80)
+    for q in (0, 1, 5, 31, 64, 80):
+        assert np.array_equal(got[q], O.x2pow(O.MT32, q)[:nw]), q
+
+
+@pytest.mark.slow
+def test_library_full_chain_matches_oracle(L, oracle_polys):
+    mu = O.minpoly(O.MT64)
+    t = time.time()
+    got = vmt.poly_x2pow(mu[:313], 19933, 19937)
+    for i, q in enumerate(range(19933, 19938)):
+        assert np.array_equal(got[i], O.x2pow(O.MT64, q)[:313]), q
+    assert time.time() - t < 120

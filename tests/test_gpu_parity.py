@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer outputs must match bit for bit; float outputs are exact conversions of
+the same bits, so they must match exactly too (tolerance 0).  Small cases are
+compared element by element over several blocks with ragged tails; the
+full-size workloads are compared on sampled generators (first, last and a
+seeded random sample), each checked over its whole output.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_16682_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+VNAME = {O.MT32: "mt32", O.MT64: "mt64", O.SFMT: "sfmt"}
+VID = {v: k for k, v in VNAME.items()}
+
+
+@pytest.fixture(scope="module")
+def vmt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_16682_gb300 as m
+    from paper_2309_16682_gb300 import build
+    build.build()
+    m.lib()
+    return m
+
+
+def _np(t):
+    if t.dtype == torch.uint32:
+        return t.cpu().view(torch.int32).numpy().view(np.uint32)
+    if t.dtype == torch.uint64:
+        return t.cpu().view(torch.int64).numpy().view(np.uint64)
+    return t.cpu().numpy()
+
+
+def _expected(variant, M, seed, segments, d=0, lanes=None):
+    """Oracle outputs for consecutive segments [(n, dtype), ...] from word 0."""
+    out, w = [], 0
+    lanes = lanes if lanes is not None else O.lane_states(variant, M, seed, d)
+    total_words = sum(n * O.words_per_output(variant, dt) for n, dt in segments)
+    words = O.vstream_words(variant, M, seed, total_words, 0, lanes=lanes)
+    for n, dt in segments:
+        k = n * O.words_per_output(variant, dt)
+        out.append(O.convert(variant, words[w:w + k], dt))
+        w += k
+    return out
+
+
+def _assert_same(got, ref, what):
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    assert got.shape == ref.shape, (what, got.shape, ref.shape)
+    bad = np.nonzero(got != ref)[0]
+    assert bad.size == 0, f"{what}: {bad.size} mismatches, first at {bad[:5]}: got {got[bad[:3]]} want {ref[bad[:3]]}"
+
+
+def test_workload_vmt32_m4_single_full(vmt, oracle_polys):
+    """The 4-lane single-generator workload, compared word for word (2^20 u32)."""
+    g = vmt.VGenerator("mt32", 4, [5489])
+    got = _np(g.generate(1 << 20, "u32"))[0]
+    assert int(got[9999 * 4]) == 4123659995   # lane 0's 10000th output
+    ref = _expected(O.MT32, 4, 5489, [(1 << 20, "u32")])[0]
+    _assert_same(got, ref, "vmt32_m4")
+
+
+def test_vmt64_m8_lane0_10000th(vmt, oracle_polys):
+    g = vmt.VGenerator("mt64", 8, [5489])
+    got = _np(g.generate(10000 * 8, "u64"))[0]
+    assert int(got[9999 * 8]) == 9981545732273789042
+
+
+@pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])
+@pytest.mark.parametrize("M", [1, 2, 4, 8, 16])
+def test_ragged_resumed_calls(vmt, oracle_polys, variant, M):
+    """Several generators, calls of awkward sizes that resume mid-block."""
+    seeds = I.splitmix64(100 + M, 3)
+    B = O.N_UNITS[variant] * M * O.WORDS_PER_UNIT[variant]
+    native = "u64" if variant == O.MT64 else "u32"
+    sizes = [1, max(1, M - 1), B + 1, B - 3, 2 * B + 5, 7]
+    segs = [(n, native) for n in sizes]
+    g = vmt.VGenerator(VNAME[variant], M, seeds)
+    got = [_np(g.generate(n, dt)) for n, dt in segs]
+    for gi, s in enumerate(seeds):
+        ref = _expected(variant, M, int(s), segs)
+        for k in range(len(segs)):
+            _assert_same(got[k][gi], ref[k], f"{VNAME[variant]} M={M} gen {gi} call {k}")
+
+
+@pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])
+def test_all_output_types_and_fused_segments(vmt, oracle_polys, variant):
+    M = 4
+    seeds = I.splitmix64(7, 2)
+    dts = ["u64", "f64", "f32"] if variant == O.MT64 else ["u32", "f32", "u64", "f64"]
+    segs = [(1000 + 8 * i, dt) for i, dt in enumerate(dts)]
+    # plain calls, one type at a time
+    g = vmt.VGenerator(VNAME[variant], M, seeds)
+    got = [_np(g.generate(n, dt)) for n, dt in segs]
+    # the same segments fused into one pass on a fresh generator
+    g2 = vmt.VGenerator(VNAME[variant], M, seeds)
+    fused = [_np(t) for t in g2.generate_multi(segs)]
+    for gi, s in enumerate(seeds):
+        ref = _expected(variant, M, int(s), segs)
+        for k, (n, dt) in enumerate(segs):
+            _assert_same(got[k][gi], ref[k], f"{VNAME[variant]} {dt} gen {gi}")
+            _assert_same(fused[k][gi], ref[k], f"{VNAME[variant]} fused {dt} gen {gi}")
+
+
+@pytest.mark.parametrize("variant", [O.MT32, O.SFMT])
+def test_pairs_at_odd_offsets(vmt, oracle_polys, variant):
+    """u64/f64 from 32-bit words starting at an odd word (generic path)."""
+    M = 2
+    g = vmt.VGenerator(VNAME[variant], M, [11])
+    a = _np(g.generate(3, "u32"))
+    b = _np(g.generate(501, "f64"))
+    c = _np(g.generate(77, "u64"))
+    ref = _expected(variant, M, 11, [(3, "u32"), (501, "f64"), (77, "u64")])
+    _assert_same(a[0], ref[0], "head")
+    _assert_same(b[0], ref[1], "f64 odd")
+    _assert_same(c[0], ref[2], "u64 odd")
+
+
+def test_single_lane_pairs(vmt, oracle_polys):
+    g = vmt.VGenerator("mt32", 1, [5])
+    b = _np(g.generate(999, "f64"))
+    ref = _expected(O.MT32, 1, 5, [(999, "f64")])
+    _assert_same(b[0], ref[0], "mt32 M=1 f64")
+
+
+@pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])
+def test_init_with_jump_offsets(vmt, oracle_polys, variant):
+    M = 4
+    seeds = np.array([1, 2, 3], np.uint64)
+    jumps = np.array([0, 123456789, 2**64 - 1], np.uint64)
+    g = vmt.VGenerator(VNAME[variant], M, seeds, jumps)
+    n = 2000
+    native = "u64" if variant == O.MT64 else "u32"
+    got = _np(g.generate(n, native))
+    for gi in range(3):
+        ref = _expected(variant, M, int(seeds[gi]), [(n, native)], d=int(jumps[gi]))[0]
+        _assert_same(got[gi], ref, f"{VNAME[variant]} d={int(jumps[gi])}")
+
+
+@pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])
+def test_jump_call_and_jump_poly(vmt, oracle_polys, variant):
+    """vmt_jump with the library's own x^d polynomial, mid-stream."""
+    M = 2
+    g = vmt.VGenerator(VNAME[variant], M, [42])
+    native = "u64" if variant == O.MT64 else "u32"
+    _ = g.generate(5, native)
+    d = 987654321
+    p = vmt.jump_poly(VNAME[variant], d)
+    assert np.array_equal(p, O.xpow(variant, d)[:p.size])
+    g.jump(p)
+    got = _np(g.generate(3000, native))[0]
+    lanes = [O.jump(st, O.xpow(variant, d)) for st in O.lane_states(variant, M, 42)]
+    words = O.vstream_words(variant, M, 42, 5 + 3000, 0, lanes=lanes)
+    # the jump advances every lane; the stream position inside the block is kept
+    _assert_same(got, words[5:], "after vmt_jump")
+
+
+def test_export_import_resume(vmt, oracle_polys):
+    g = vmt.VGenerator("mt32", 8, I.splitmix64(3, 4))
+    _ = g.generate(777, "u32")
+    blob = g.export_state()
+    a = _np(g.generate(20000, "u32"))
+    g2 = vmt.VGenerator("mt32", 8, I.splitmix64(99, 4))
+    g2.import_state(blob)
+    b = _np(g2.generate(20000, "u32"))
+    assert np.array_equal(a, b)
+    bad = bytearray(blob)
+    bad[0] ^= 1
+    with pytest.raises(vmt.VMTError):
+        g2.import_state(bytes(bad))
+
+
+def test_generate_host_matches_device(vmt, oracle_polys):
+    seeds = I.splitmix64(5, 6)
+    g1 = vmt.VGenerator("mt32", 16, seeds)
+    g2 = vmt.VGenerator("mt32", 16, seeds)
+    d = _np(g1.generate(100003, "f32"))
+    h = g2.generate_host(100003, "f32").numpy()
+    assert np.array_equal(d, h)
+
+
+def test_zero_and_empty_calls(vmt, oracle_polys):
+    g = vmt.VGenerator("sfmt", 4, [9])
+    _ = g.generate(0, "u32")
+    got = _np(g.generate(100, "u32"))[0]
+    ref = _expected(O.SFMT, 4, 9, [(100, "u32")])[0]
+    _assert_same(got, ref, "after empty call")
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads: sampled generators, whole outputs
+# ---------------------------------------------------------------------------
+def _sample(count, k=6, seed=0):
+    rng = np.random.default_rng(seed)
+    s = {0, count - 1}
+    s.update(int(x) for x in rng.integers(0, count, k))
+    return sorted(s)
+
+
+@pytest.mark.parametrize("name", ["vmt32_m16_g65536", "vmt64_m8_g32768", "vsfmt_m4_g16384"])
+def test_full_workloads_sampled(vmt, oracle_polys, name):
+    w = I.WORKLOADS[name]
+    variant = VID[w["variant"]]
+    seeds = I.workload_seeds(name)
+    g = vmt.VGenerator(w["variant"], w["lanes"], seeds)
+    count = w["generators"]
+    segs = [(n // count, dt) for dt, n in w["outputs"]]
+    outs = g.generate_multi(segs)
+    torch.cuda.synchronize()
+    for gi in _sample(count, seed=len(name)):
+        ref = _expected(variant, w["lanes"], int(seeds[gi]), segs)
+        for k, (n, dt) in enumerate(segs):
+            _assert_same(_np(outs[k][gi]), ref[k], f"{name} gen {gi} seg {k}")
+    del outs
+    torch.cuda.empty_cache()
