@@ -209,11 +209,11 @@ def run_gb300(args, world, rank, local):
     import torch
     import paper_2309_16682_gb300 as vmt
     w = I.WORKLOADS[args.workload]
-    count = w["generators"]
-    segs = [(n // count, dt) for dt, n in w["outputs"]]
+    segs = [(n // w["generators"], dt) for dt, n in w["outputs"]]   # outputs per generator
+    count = args.generators or w["generators"]
     esize = {"u32": 4, "f32": 4, "u64": 8, "f64": 8}
     out_bytes = sum(n * count * esize[dt] for n, dt in segs)
-    seeds = I.workload_seeds(args.workload)
+    seeds = I.workload_seeds(args.workload)[:count]
     if rank:
         seeds = I.splitmix64(1000003 * rank + 1, count)  # each rank: its own generators
     stream = torch.cuda.current_stream()
@@ -291,7 +291,8 @@ def run_gb300(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": args.workload, "variant": w["variant"], "lanes": w["lanes"],
+            "config": {"workload": args.workload if not args.generators else f"{args.workload}[:{count}]",
+                       "variant": w["variant"], "lanes": w["lanes"],
                        "generators_per_gpu": count, "outputs_per_step": [[dt, n * count] for n, dt in segs],
                        "l2": "no flush: each step writes %.1f GiB (> 129 MB L2)" % (out_bytes / 2**30),
                        "parallelism": f"{world} independent GPU(s), generators sharded, no collective"},
@@ -320,6 +321,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="vmt32_m16_g65536", choices=sorted(I.WORKLOADS))
     ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--generators", type=int, default=0,
+                    help="smaller generator count (profiling cases); default: the workload's")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
