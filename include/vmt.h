@@ -175,6 +175,33 @@ int vmt_poly_minpoly(const uint64_t* bits, int64_t n, uint64_t* mu_out, int64_t 
 int vmt_poly_mulmod(const uint64_t* a, const uint64_t* b, const uint64_t* mu, uint64_t* out, int64_t nw);
 int vmt_poly_x2pow(const uint64_t* mu, int64_t nw, int q_lo, int q_hi, uint64_t* out);
 
+/*
+ * vmt_jump_noalloc -- vmt_jump for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a deployment variant of vmt_jump.
+ *
+ * vmt_jump allocates device scratch on every call (a polynomial row and a
+ * table of lane-jump work items).  Some callers cannot do that: code running
+ * while a framework's caching allocator holds all free HBM, latency-bound loops
+ * that must not pay for cudaMalloc/cudaFree, or plug-ins whose host forbids
+ * library allocations.  This entry point computes the same result as vmt_jump
+ * (st, poly and nbits mean the same) but calls no cudaMalloc, cudaFree or other
+ * allocating routine: its scratch is a static device array of about 515 KiB
+ * inside libvmt.so, which every GPU that loads the library keeps until the
+ * process exits.
+ *   - count * lanes of st must not exceed VMT_NOALLOC_MAX_LANE_STATES; larger
+ *     states are rejected with VMT_EINVAL (nothing is enqueued);
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - all calls share the one array: calls whose work overlaps on the GPU
+ *     (different streams without ordering) race on it; order them on one
+ *     stream or with events;
+ *   - the caller's poly is read before the call returns (when nbits is not a
+ *     multiple of 64 the call also waits for `cuda_stream`).
+ */
+#define VMT_NOALLOC_MAX_LANE_STATES 16384
+int vmt_jump_noalloc(vmt_state* st, const uint64_t* poly, int64_t nbits, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

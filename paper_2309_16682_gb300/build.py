@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libvmt.so")
 
-CUDA_SOURCES = ["gen_mt.cu", "gen_sfmt.cu", "jump.cu", "vmt_capi.cu"]
+CUDA_SOURCES = ["gen_mt.cu", "gen_sfmt.cu", "jump.cu", "vmt_capi.cu", "noalloc.cu"]
 CXX_SOURCES = ["gf2poly.cpp"]
 HEADERS = ["vmt_device.cuh", "vmt_internal.hpp", "gf2poly.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -37,8 +37,12 @@ cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, cudaStream
 using vmt::gf2::Poly;
 
 namespace {
-
 thread_local std::string g_err;
+}
+
+void vmt::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+namespace {
 
 int fail(int code, const std::string& msg)
 {

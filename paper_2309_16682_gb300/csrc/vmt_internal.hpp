@@ -57,6 +57,8 @@ constexpr int kPolyWords = 640;  // u32 words per polynomial row (20480 bits)
 cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, cudaStream_t s);
 cudaError_t launch_seed(int variant, long long count, const unsigned long long* seeds, void* base, cudaStream_t s);
 cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s);
-cudaError_t launch_copy_lane(int variant, int lanes, long long gens, const void* base, void* states, cudaStream_t s);
+
+// message returned by vmt_last_error() on this thread
+void set_last_error(const char* msg);
 
 }  // namespace vmt
