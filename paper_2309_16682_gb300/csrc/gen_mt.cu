@@ -57,94 +57,409 @@ __device__ __forceinline__ void emit_words(const Emitter& em, long long f0, cons
     em.emit64<VW>(f0, z, lo, hi, ebase);
 }
 
-template <class G, int M, int VW, int T>
+// Bytes of output per native word for an output type: 32-bit words give 4
+// (u32, f32, and u64/f64 built from two words); 64-bit words give 8 (u64,
+// f64) or 4 (f32).
+template <typename W>
+__device__ __forceinline__ int bytes_per_word(int dt)
+{
+    return (sizeof(W) == 4 || dt == VMT_F32) ? 4 : 8;
+}
+
+// Output plan of one block, spread over the lanes of every warp: lane s holds
+// segment s (base address such that block word f goes to base + f * bpw, and
+// its output type); every lane holds the block-coordinate segment boundaries.
+// A 16-byte vector at block word f0 then needs three compares and two shuffles
+// to find its segment and address.
+struct BlockPlan {
+    long long my_base;
+    int my_dt;
+    int b1, b2, b3;
+    bool fast;   // every segment base aligned to a vector and every boundary on a vector
+
+    template <class P, typename W, int VW>
+    __device__ __forceinline__ void make(const GenArgs& a, long long g, long long delta)
+    {
+        const int lane = threadIdx.x & 31;
+        int bnd = 0x7FFFFFFF;
+        bool ok = true;
+        my_base = 0;
+        my_dt = VMT_U32;
+        if (lane < a.nseg) {
+            const SegArg& sg = a.seg[lane];
+            const int bpw = bytes_per_word<W>(sg.dtype);
+            const int esz = (sg.dtype == VMT_U32 || sg.dtype == VMT_F32) ? 4 : 8;
+            my_dt = sg.dtype;
+            my_base = reinterpret_cast<long long>(sg.out) + g * sg.count * esz + (delta - sg.wbeg) * bpw;
+            ok = (my_base % (VW * bpw)) == 0;
+            long long b = sg.wbeg - delta;   // block word where the segment starts
+            if (b < -1) b = -1;
+            if (b > (1LL << 30)) b = 1LL << 30;
+            bnd = static_cast<int>(b);
+            if (b > 0 && b < (1LL << 30) && (b % VW) != 0) ok = false;
+        }
+        fast = __all_sync(0xFFFFFFFFu, ok);
+        b1 = __shfl_sync(0xFFFFFFFFu, bnd, 1);
+        b2 = __shfl_sync(0xFFFFFFFFu, bnd, 2);
+        b3 = __shfl_sync(0xFFFFFFFFu, bnd, 3);
+        if (a.nseg < 2) b1 = 0x7FFFFFFF;
+        if (a.nseg < 3) b2 = 0x7FFFFFFF;
+        if (a.nseg < 4) b3 = 0x7FFFFFFF;
+    }
+};
+
+// store VW tempered words at block word f0 (fast path; the whole vector is in
+// range, in one segment and aligned).  Executed by all lanes of the warp (the
+// shuffles need them); `doit` masks the store.
+template <typename W, int VW>
+__device__ __forceinline__ void plan_store(const BlockPlan& P, int f0, const W (&z)[VW], bool doit)
+{
+    const int s = (f0 >= P.b1) + (f0 >= P.b2) + (f0 >= P.b3);
+    const long long base = __shfl_sync(0xFFFFFFFFu, P.my_base, s);
+    const int dt = __shfl_sync(0xFFFFFFFFu, P.my_dt, s);
+    if (!doit) return;
+    if (sizeof(W) == 4) {
+        const uint32_t* u = reinterpret_cast<const uint32_t*>(z);
+        char* ptr = reinterpret_cast<char*>(base + 4LL * f0);
+        if (VW == 4) {
+            if (dt == VMT_U32) __stcs(reinterpret_cast<uint4*>(ptr), make_uint4(u[0], u[1 % VW], u[2 % VW], u[3 % VW]));
+            else if (dt == VMT_F32)
+                __stcs(reinterpret_cast<float4*>(ptr), make_float4(f32_of_u32(u[0]), f32_of_u32(u[1 % VW]),
+                                                                   f32_of_u32(u[2 % VW]), f32_of_u32(u[3 % VW])));
+            else if (dt == VMT_U64) {
+                ulonglong2 v;
+                v.x = static_cast<unsigned long long>(u[0]) | (static_cast<unsigned long long>(u[1 % VW]) << 32);
+                v.y = static_cast<unsigned long long>(u[2 % VW]) | (static_cast<unsigned long long>(u[3 % VW]) << 32);
+                __stcs(reinterpret_cast<ulonglong2*>(ptr), v);
+            } else {
+                double2 v;
+                v.x = f64_of_pair(u[0], u[1 % VW]);
+                v.y = f64_of_pair(u[2 % VW], u[3 % VW]);
+                __stcs(reinterpret_cast<double2*>(ptr), v);
+            }
+        } else if (VW == 2) {
+            if (dt == VMT_U32) __stcs(reinterpret_cast<uint2*>(ptr), make_uint2(u[0], u[1 % VW]));
+            else if (dt == VMT_F32) __stcs(reinterpret_cast<float2*>(ptr), make_float2(f32_of_u32(u[0]), f32_of_u32(u[1 % VW])));
+            else if (dt == VMT_U64)
+                __stcs(reinterpret_cast<unsigned long long*>(ptr),
+                       static_cast<unsigned long long>(u[0]) | (static_cast<unsigned long long>(u[1 % VW]) << 32));
+            else __stcs(reinterpret_cast<double*>(ptr), f64_of_pair(u[0], u[1 % VW]));
+        } else {
+            if (dt == VMT_U32) __stcs(reinterpret_cast<uint32_t*>(ptr), u[0]);
+            else if (dt == VMT_F32) __stcs(reinterpret_cast<float*>(ptr), f32_of_u32(u[0]));
+        }
+    } else {
+        const unsigned long long* u = reinterpret_cast<const unsigned long long*>(z);
+        if (dt == VMT_F32) {
+            char* ptr = reinterpret_cast<char*>(base + 4LL * f0);
+            if (VW == 2) __stcs(reinterpret_cast<float2*>(ptr), make_float2(f32_of_u64(u[0]), f32_of_u64(u[1 % VW])));
+            else __stcs(reinterpret_cast<float*>(ptr), f32_of_u64(u[0]));
+        } else {
+            char* ptr = reinterpret_cast<char*>(base + 8LL * f0);
+            if (VW == 2) {
+                if (dt == VMT_U64) {
+                    ulonglong2 v;
+                    v.x = u[0];
+                    v.y = u[1 % VW];
+                    __stcs(reinterpret_cast<ulonglong2*>(ptr), v);
+                } else {
+                    double2 v;
+                    v.x = f64_of_u64(u[0]);
+                    v.y = f64_of_u64(u[1 % VW]);
+                    __stcs(reinterpret_cast<double2*>(ptr), v);
+                }
+            } else {
+                if (dt == VMT_U64) __stcs(reinterpret_cast<unsigned long long*>(ptr), u[0]);
+                else __stcs(reinterpret_cast<double*>(ptr), f64_of_u64(u[0]));
+            }
+        }
+    }
+}
+
+// Emit the vector of VW tempered words at block word f0 whose valid block
+// range is [lo, hi); delta converts block words to call words.
+template <typename W, int VW>
+__device__ __forceinline__ void emit_vec(const BlockPlan& P, const Emitter& em, int f0, const W (&z)[VW], int lo,
+                                         int hi, long long delta, bool active)
+{
+    const bool full = active && f0 >= lo && f0 + VW <= hi;
+    if (P.fast) {
+        plan_store<W, VW>(P, f0, z, full);
+        if (full || !active) return;
+    }
+    if (active) emit_words<VW>(em, f0, z, lo, hi, delta + lo);
+}
+
+// Output policy: the output types of a call known at compile time (one
+// segment, or two segments split at a run-time boundary), or GENERIC (any
+// segment list, resolved per vector through BlockPlan).
+template <int DT0_, int DT1_>
+struct Pol {
+    static constexpr int DT0 = DT0_, DT1 = DT1_;
+    static constexpr bool generic = DT0_ < 0;
+    static constexpr int nseg = generic ? 0 : (DT1_ < 0 ? 1 : 2);
+};
+using PolGeneric = Pol<-1, -1>;
+
+// store VW words of one statically typed segment at base + f0 * bytes_per_word
+template <int DT, typename W, int VW>
+__device__ __forceinline__ void store_typed(long long base, int f0, const W (&z)[VW])
+{
+    if constexpr (sizeof(W) == 4) {
+        const uint32_t* u = reinterpret_cast<const uint32_t*>(z);
+        char* ptr = reinterpret_cast<char*>(base + 4LL * f0);
+        if constexpr (VW == 4) {
+            if constexpr (DT == VMT_U32) __stcs(reinterpret_cast<uint4*>(ptr), make_uint4(u[0], u[1], u[2], u[3]));
+            if constexpr (DT == VMT_F32)
+                __stcs(reinterpret_cast<float4*>(ptr),
+                       make_float4(f32_of_u32(u[0]), f32_of_u32(u[1]), f32_of_u32(u[2]), f32_of_u32(u[3])));
+            if constexpr (DT == VMT_U64) {
+                ulonglong2 v;
+                v.x = static_cast<unsigned long long>(u[0]) | (static_cast<unsigned long long>(u[1]) << 32);
+                v.y = static_cast<unsigned long long>(u[2]) | (static_cast<unsigned long long>(u[3]) << 32);
+                __stcs(reinterpret_cast<ulonglong2*>(ptr), v);
+            }
+            if constexpr (DT == VMT_F64) {
+                double2 v;
+                v.x = f64_of_pair(u[0], u[1]);
+                v.y = f64_of_pair(u[2], u[3]);
+                __stcs(reinterpret_cast<double2*>(ptr), v);
+            }
+        }
+    } else {
+        const unsigned long long* u = reinterpret_cast<const unsigned long long*>(z);
+        if constexpr (VW == 2) {
+            if constexpr (DT == VMT_F32)
+                __stcs(reinterpret_cast<float2*>(reinterpret_cast<char*>(base + 4LL * f0)),
+                       make_float2(f32_of_u64(u[0]), f32_of_u64(u[1])));
+            if constexpr (DT == VMT_U64) {
+                ulonglong2 v;
+                v.x = u[0];
+                v.y = u[1];
+                __stcs(reinterpret_cast<ulonglong2*>(reinterpret_cast<char*>(base + 8LL * f0)), v);
+            }
+            if constexpr (DT == VMT_F64) {
+                double2 v;
+                v.x = f64_of_u64(u[0]);
+                v.y = f64_of_u64(u[1]);
+                __stcs(reinterpret_cast<double2*>(reinterpret_cast<char*>(base + 8LL * f0)), v);
+            }
+        }
+    }
+}
+
+// Per-block plan for a static policy: segment bases and the boundary in block
+// words; ok when both bases are vector-aligned and the boundary falls on a vector.
+struct TypedPlan {
+    long long base0, base1;
+    int b1;
+    bool ok;
+
+    template <class P, typename W, int VW>
+    __device__ __forceinline__ void make(const GenArgs& a, long long g, long long delta)
+    {
+        const int bpw0 = bytes_per_word<W>(P::DT0);
+        const int esz0 = (P::DT0 == VMT_U32 || P::DT0 == VMT_F32) ? 4 : 8;
+        base0 = reinterpret_cast<long long>(a.seg[0].out) + g * a.seg[0].count * esz0 + (delta - a.seg[0].wbeg) * bpw0;
+        ok = (base0 % (VW * bpw0)) == 0;
+        b1 = 0x7FFFFFFF;
+        base1 = 0;
+        if constexpr (P::nseg == 2) {
+            const int bpw1 = bytes_per_word<W>(P::DT1);
+            const int esz1 = (P::DT1 == VMT_U32 || P::DT1 == VMT_F32) ? 4 : 8;
+            base1 = reinterpret_cast<long long>(a.seg[1].out) + g * a.seg[1].count * esz1 + (delta - a.seg[1].wbeg) * bpw1;
+            ok = ok && (base1 % (VW * bpw1)) == 0;
+            long long b = a.seg[1].wbeg - delta;
+            if (b < -1) b = -1;
+            if (b > (1LL << 30)) b = 1LL << 30;
+            b1 = static_cast<int>(b);
+            if (b > 0 && b < (1LL << 30) && (b % VW) != 0) ok = false;
+        }
+    }
+};
+
+template <class P>
+struct PlanOf {
+    using type = TypedPlan;
+};
+template <>
+struct PlanOf<PolGeneric> {
+    using type = BlockPlan;
+};
+
+// Emit the vector at block word f0 (valid block range [lo, hi); block word f
+// is call word f + delta).  `check` is false when the whole vector is known to
+// be in range.  All lanes call this (the generic plan shuffles).
+template <class P, typename W, int VW>
+__device__ __forceinline__ void emit_p(const typename PlanOf<P>::type& plan, const Emitter& em, int f0,
+                                       const W (&z)[VW], int lo, int hi, long long delta, bool active, bool check)
+{
+    const bool full = active && (!check || (f0 >= lo && f0 + VW <= hi));
+    if constexpr (P::generic) {
+        if (plan.fast) {
+            plan_store<W, VW>(plan, f0, z, full);
+            if (full || !active) return;
+        }
+        if (active) emit_words<VW>(em, f0, z, lo, hi, delta + lo);
+    } else {
+        if (full && plan.ok) {
+            if (P::nseg == 1 || f0 < plan.b1) store_typed<P::DT0, W, VW>(plan.base0, f0, z);
+            else store_typed<(P::nseg == 2 ? P::DT1 : P::DT0), W, VW>(plan.base1, f0, z);
+        } else if (active) {
+            emit_words<VW>(em, f0, z, lo, hi, delta + lo);
+        }
+    }
+}
+
+// One phase of the block twist: rows [K0, K1), reading the old block `cur`
+// and the rows of `nxt` finished by earlier phases.
+template <class G, int M, int VW, int T, class P, int K0, int K1>
+__device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G::W* nxt,
+                                            const typename PlanOf<P>::type& plan, const Emitter& em, int hi,
+                                            long long e, bool check)
+{
+    using W = typename G::W;
+    constexpr int N = G::N, MM = G::MM, NM = N - MM;
+    constexpr int RV = M / VW, NV = N * RV;
+    constexpr int V0 = K0 * RV, V1 = K1 * RV;
+    constexpr int ITEMS = (V1 - V0 + T - 1) / T;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int v = V0 + tid + i * T;
+        const bool act = ((i + 1) * T <= V1 - V0) || v < V1;   // static for all but the last item
+        W nw[VW], z[VW];
+        if (act) {
+            W xa[VW], xb[VW], xc[VW];
+            ldv<W, VW>(cur + v * VW, xa);
+            if (K1 < N || v + RV < NV) ldv<W, VW>(cur + (v + RV) * VW, xb);   // old x_{k+1}
+            else ldv<W, VW>(nxt + (v + RV - NV) * VW, xb);                    // new x_0 for the last row
+            if (K0 == 0) ldv<W, VW>(cur + (v + MM * RV) * VW, xc);          // old x_{k+m}
+            else ldv<W, VW>(nxt + (v - NM * RV) * VW, xc);                  // new x_{k-(n-m)}
+#pragma unroll
+            for (int u = 0; u < VW; ++u) {
+                nw[u] = G::twist(xa[u], xb[u], xc[u]);
+                z[u] = G::temper(nw[u]);
+            }
+            stv<W, VW>(nxt + v * VW, nw);
+        } else {
+#pragma unroll
+            for (int u = 0; u < VW; ++u) z[u] = W(0);
+        }
+        emit_p<P, W, VW>(plan, em, v * VW, z, 0, hi, e, act, check);
+    }
+}
+
+template <class G, int M, int VW, int T, class P>
 __global__ void __launch_bounds__(T) gen_mt_kernel(GenArgs a)
 {
     using W = typename G::W;
     constexpr int N = G::N, MM = G::MM, NM = N - MM;
     constexpr int B = N * M;        // words per block
-    constexpr int RV = M / VW;      // vectors per row
     constexpr int NV = B / VW;      // vectors per block
-    constexpr int ITEMS = (NM * RV + T - 1) / T;
-    __shared__ __align__(16) W s[B];
+    static_assert(N <= 3 * NM, "at most three phases");
+    // two copies of X-hat: the old block is only read while the new one is
+    // written, so a phase needs no barrier between its loads and its stores
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    W* const buf0 = reinterpret_cast<W*>(smem_raw);
+    W* const buf1 = buf0 + B;
+    const int tid = threadIdx.x;
+    using Plan = typename PlanOf<P>::type;
 
     for (long long gi = blockIdx.x; gi < a.gens; gi += gridDim.x) {
         W* gst = reinterpret_cast<W*>(a.states) + gi * static_cast<long long>(B);
-        for (int v = threadIdx.x; v < NV; v += T) {
+        W* cur = buf0;
+        W* nxt = buf1;
+        for (int v = tid; v < NV; v += T) {
             W w[VW];
             ldv<W, VW>(gst + v * VW, w);
-            stv<W, VW>(s + v * VW, w);
+            stv<W, VW>(cur + v * VW, w);
         }
         __syncthreads();
-        const Emitter em{a, a.gen0 + gi};
-        long long e = 0;
-        const long long p = a.pos;
-        if (p < B && a.total > 0) {
-            // rest of the current block
-            const long long hi = min(static_cast<long long>(B), p + a.total);
-            for (long long v = p / VW + threadIdx.x; v * VW < hi; v += T) {
+        const long long g = a.gen0 + gi;
+        const Emitter em{a, g};
+        const int total = static_cast<int>(a.total);
+        int e = 0;
+        const int p = a.pos;
+        Plan plan;
+        if (p < B && total > 0) {
+            // rest of the current block: block word f is call word f - p
+            const int hi = min(B, p + total);
+            plan.template make<P, W, VW>(a, g, -static_cast<long long>(p));
+            for (int v0 = p / VW; v0 * VW < hi; v0 += T) {
+                const int v = v0 + tid;
                 W w[VW], z[VW];
-                ldv<W, VW>(s + v * VW, w);
+                const bool act = v * VW < hi;
+                if (act) ldv<W, VW>(cur + v * VW, w);
 #pragma unroll
-                for (int u = 0; u < VW; ++u) z[u] = G::temper(w[u]);
-                emit_words<VW>(em, v * VW, z, p, hi, 0);
+                for (int u = 0; u < VW; ++u) z[u] = act ? G::temper(w[u]) : W(0);
+                emit_p<P, W, VW>(plan, em, v * VW, z, p, hi, -static_cast<long long>(p), act, true);
             }
             e = hi - p;
         }
-        while (e < a.total) {
-            const long long hi = min(static_cast<long long>(B), a.total - e);
-#pragma unroll 1
-            for (int k0 = 0; k0 < N; k0 += NM) {
-                const int k1 = min(k0 + NM, N);
-                const int v0 = k0 * RV, v1 = k1 * RV;
-                W xa[ITEMS][VW], xb[ITEMS][VW], xc[ITEMS][VW];
-#pragma unroll
-                for (int i = 0; i < ITEMS; ++i) {
-                    const int v = v0 + static_cast<int>(threadIdx.x) + i * T;
-                    if (v < v1) {
-                        ldv<W, VW>(s + v * VW, xa[i]);
-                        int vb = v + RV;
-                        if (vb >= NV) vb -= NV;   // x_{n} of the last row is the new x_0
-                        ldv<W, VW>(s + vb * VW, xb[i]);
-                        const int vc = (k0 == 0) ? v + MM * RV : v - NM * RV;
-                        ldv<W, VW>(s + vc * VW, xc[i]);
-                    }
-                }
-                __syncthreads();
-#pragma unroll
-                for (int i = 0; i < ITEMS; ++i) {
-                    const int v = v0 + static_cast<int>(threadIdx.x) + i * T;
-                    if (v < v1) {
-                        W nw[VW], z[VW];
-#pragma unroll
-                        for (int u = 0; u < VW; ++u) {
-                            nw[u] = G::twist(xa[i][u], xb[i][u], xc[i][u]);
-                            z[u] = G::temper(nw[u]);
-                        }
-                        stv<W, VW>(s + v * VW, nw);
-                        emit_words<VW>(em, static_cast<long long>(v) * VW, z, 0, hi, e);
-                    }
-                }
+        while (e < total) {
+            const int hi = min(B, total - e);   // block words [0, hi) are emitted
+            const bool check = hi < B;
+            plan.template make<P, W, VW>(a, g, e);
+            twist_phase<G, M, VW, T, P, 0, NM>(cur, nxt, plan, em, hi, e, check);
+            __syncthreads();
+            twist_phase<G, M, VW, T, P, NM, (2 * NM < N ? 2 * NM : N)>(cur, nxt, plan, em, hi, e, check);
+            __syncthreads();
+            if constexpr (2 * NM < N) {
+                twist_phase<G, M, VW, T, P, (2 * NM < N ? 2 * NM : N), N>(cur, nxt, plan, em, hi, e, check);
                 __syncthreads();
             }
+            W* t = cur;
+            cur = nxt;
+            nxt = t;
             e += hi;
         }
-        for (int v = threadIdx.x; v < NV; v += T) {
+        for (int v = tid; v < NV; v += T) {
             W w[VW];
-            ldv<W, VW>(s + v * VW, w);
+            ldv<W, VW>(cur + v * VW, w);
             stv<W, VW>(gst + v * VW, w);
         }
         __syncthreads();
     }
 }
 
+template <class G, int M, int VW, int T, class P>
+static cudaError_t launch_mt_p(const GenArgs& a, cudaStream_t st)
+{
+    constexpr int smem = 2 * G::N * M * static_cast<int>(sizeof(typename G::W));
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(gen_mt_kernel<G, M, VW, T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const long long grid = a.gens < (1LL << 30) ? a.gens : (1LL << 30);
+    gen_mt_kernel<G, M, VW, T, P><<<static_cast<unsigned>(grid), T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// policy dispatch: typed kernels for the common type patterns, generic otherwise
 template <class G, int M, int VW, int T>
 static cudaError_t launch_mt(const GenArgs& a, cudaStream_t st)
 {
     if (a.gens <= 0) return cudaSuccess;
-    const long long grid = a.gens < (1LL << 30) ? a.gens : (1LL << 30);
-    gen_mt_kernel<G, M, VW, T><<<static_cast<unsigned>(grid), T, 0, st>>>(a);
-    return cudaGetLastError();
+    if constexpr (M >= 4) {
+        const int d0 = a.seg[0].dtype, d1 = a.nseg > 1 ? a.seg[1].dtype : -1;
+        if constexpr (sizeof(typename G::W) == 4) {
+            if (a.nseg == 1 && d0 == VMT_U32) return launch_mt_p<G, M, VW, T, Pol<VMT_U32, -1>>(a, st);
+            if (a.nseg == 1 && d0 == VMT_F32) return launch_mt_p<G, M, VW, T, Pol<VMT_F32, -1>>(a, st);
+            if (a.nseg == 1 && d0 == VMT_F64) return launch_mt_p<G, M, VW, T, Pol<VMT_F64, -1>>(a, st);
+            if (a.nseg == 2 && d0 == VMT_U32 && d1 == VMT_F32)
+                return launch_mt_p<G, M, VW, T, Pol<VMT_U32, VMT_F32>>(a, st);
+        } else {
+            if (a.nseg == 1 && d0 == VMT_U64) return launch_mt_p<G, M, VW, T, Pol<VMT_U64, -1>>(a, st);
+            if (a.nseg == 1 && d0 == VMT_F64) return launch_mt_p<G, M, VW, T, Pol<VMT_F64, -1>>(a, st);
+            if (a.nseg == 2 && d0 == VMT_U64 && d1 == VMT_F64)
+                return launch_mt_p<G, M, VW, T, Pol<VMT_U64, VMT_F64>>(a, st);
+        }
+    }
+    return launch_mt_p<G, M, VW, T, PolGeneric>(a, st);
 }
 
 }  // namespace dev

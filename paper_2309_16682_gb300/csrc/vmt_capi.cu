@@ -390,15 +390,19 @@ int vector_width(int variant, int lanes)
     return std::min(lanes, 2);
 }
 
-int generate_impl(vmt_state* st, int nseg, const int64_t* counts, const int* dtypes, void* const* outs,
-                  cudaStream_t s)
+// Generate `nseg` consecutive segments for generators [g0, g0 + gens) of st,
+// whose outputs start at outs[i] (generator g0 writes at outs[i] + 0).  The
+// block position is not advanced: all generator ranges of one call start at the
+// same position and the caller advances it once.
+int generate_range(vmt_state* st, int64_t g0, int64_t gens, int nseg, const int64_t* counts, const int* dtypes,
+                   void* const* outs, cudaStream_t s)
 {
     if (!st) return fail(VMT_EINVAL, "null state");
     if (nseg < 1 || nseg > VMT_MAXSEG) return fail(VMT_EINVAL, "nseg must be in 1..4");
     const int v = st->variant;
     vmt::GenArgs a{};
-    a.states = st->d_states;
-    a.gens = st->count;
+    a.states = static_cast<char*>(st->d_states) + g0 * vmt::state_bytes_per_gen(v, st->lanes);
+    a.gens = gens;
     a.gen0 = 0;
     a.pos = static_cast<int>(st->block_pos);
     a.nseg = nseg;
@@ -427,15 +431,47 @@ int generate_impl(vmt_state* st, int nseg, const int64_t* counts, const int* dty
         w += counts[i] * wpo;
     }
     a.total = w;
-    if (w == 0) return VMT_OK;
-    const int64_t B = vmt::block_words(v, st->lanes);
+    if (w == 0 || gens == 0) return VMT_OK;
+    // the kernels index words of one call with 32-bit integers: longer calls
+    // are cut into pieces of at most 2^30 words (an even number, so that no
+    // output pair is split); each piece starts where the previous one ended
+    constexpr int64_t kPiece = int64_t(1) << 30;
+    if (!generic && w > kPiece) {
+        const int64_t B = vmt::block_words(v, st->lanes);
+        int64_t pos = st->block_pos;
+        for (int64_t w0 = 0; w0 < w; w0 += kPiece) {
+            const int64_t w1 = std::min(w, w0 + kPiece);
+            vmt::GenArgs pa = a;
+            pa.pos = static_cast<int>(pos);
+            pa.total = w1 - w0;
+            pa.nseg = 0;
+            for (int i = 0; i < nseg; ++i) {
+                const vmt::SegArg& sg = a.seg[i];
+                const int64_t lo = std::max<int64_t>(sg.wbeg, w0), hi = std::min<int64_t>(sg.wend, w1);
+                if (lo >= hi) continue;
+                const int wpo = words_per_output(v, sg.dtype);
+                vmt::SegArg q = sg;
+                // outputs of generator g in this piece start at out + g*count + (lo - wbeg)/wpo;
+                // the kernel adds g*count itself
+                q.out = sg.out + ((lo - sg.wbeg) / wpo) * elem_bytes(sg.dtype);
+                q.wbeg = lo - w0;
+                q.wend = hi - w0;
+                pa.seg[pa.nseg++] = q;
+            }
+            CUDA_TRY(vmt::launch_generate(v, st->lanes, pa, s));
+            pos = new_block_pos(B, pos, w1 - w0);
+        }
+        return VMT_OK;
+    }
+    if (generic && w > kPiece)
+        return fail(VMT_EINVAL, "two-word outputs at an odd word offset are limited to 2^30 words per call");
     if (!generic) {
         CUDA_TRY(vmt::launch_generate(v, st->lanes, a, s));
     } else {
         // raw native words into scratch, then one conversion per segment
         const int wb = vmt::word_bytes(v);
         void* scratch = nullptr;
-        CUDA_TRY(cudaMallocAsync(&scratch, static_cast<size_t>(st->count * w * wb), s));
+        CUDA_TRY(cudaMallocAsync(&scratch, static_cast<size_t>(gens * w * wb), s));
         vmt::GenArgs r = a;
         r.nseg = 1;
         r.seg[0].out = static_cast<char*>(scratch);
@@ -446,11 +482,28 @@ int generate_impl(vmt_state* st, int nseg, const int64_t* counts, const int* dty
         r.seg[0].fast = 0;
         CUDA_TRY(vmt::launch_generate(v, st->lanes, r, s));
         for (int i = 0; i < nseg; ++i)
-            CUDA_TRY(vmt::launch_convert(scratch, w, v == VMT_MT19937_64, st->count, a.seg[i].wbeg, a.seg[i].dtype,
+            CUDA_TRY(vmt::launch_convert(scratch, w, v == VMT_MT19937_64, gens, a.seg[i].wbeg, a.seg[i].dtype,
                                          a.seg[i].count, a.seg[i].out, s));
         CUDA_TRY(cudaFreeAsync(scratch, s));
     }
-    st->block_pos = new_block_pos(B, st->block_pos, w);
+    return VMT_OK;
+}
+
+int64_t call_words(const vmt_state* st, int nseg, const int64_t* counts, const int* dtypes)
+{
+    int64_t w = 0;
+    for (int i = 0; i < nseg; ++i) w += counts[i] * words_per_output(st->variant, dtypes[i]);
+    return w;
+}
+
+int generate_impl(vmt_state* st, int nseg, const int64_t* counts, const int* dtypes, void* const* outs,
+                  cudaStream_t s)
+{
+    if (!st) return fail(VMT_EINVAL, "null state");
+    const int rc = generate_range(st, 0, st->count, nseg, counts, dtypes, outs, s);
+    if (rc) return rc;
+    st->block_pos = new_block_pos(vmt::block_words(st->variant, st->lanes), st->block_pos,
+                                  call_words(st, nseg, counts, dtypes));
     return VMT_OK;
 }
 
@@ -627,47 +680,64 @@ int vmt_generate_host(vmt_state* st, int64_t n, int dtype, void* out_host, void*
 {
     if (!st || (!out_host && n > 0)) return fail(VMT_EINVAL, "null argument");
     if (n < 0) return fail(VMT_EINVAL, "negative count");
+    if (dtype < VMT_U32 || dtype > VMT_F64) return fail(VMT_EINVAL, "bad dtype");
     if (n == 0) return VMT_OK;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const int eb = elem_bytes(dtype);
-    // chunk so that one staging buffer holds <= 256 MiB; two buffers alternate
-    int64_t chunk = std::max<int64_t>(1, (int64_t(256) << 20) / (eb * st->count));
-    chunk = std::min(chunk, n);
-    if (chunk > 4) chunk &= ~int64_t(3);
+    const int64_t eb = elem_bytes(dtype);
+    const int64_t row = n * eb;   // one generator's output bytes
+    const int64_t kStage = int64_t(256) << 20;
+    if (row > kStage) {
+        // very long rows: generate the whole call on the device in one pass and
+        // copy it back in one piece
+        void* buf = nullptr;
+        CUDA_TRY(cudaMallocAsync(&buf, static_cast<size_t>(row * st->count), s));
+        int rc = vmt_generate(st, n, dtype, buf, s);
+        if (rc == VMT_OK) {
+            cudaError_t e = cudaMemcpyAsync(out_host, buf, static_cast<size_t>(row * st->count), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = fail(VMT_ECUDA, cudaGetErrorString(e));
+        }
+        cudaFreeAsync(buf, s);
+        return rc;
+    }
+    // generator ranges: every range produces whole rows, so each device-to-host
+    // copy is one contiguous block; two staging buffers alternate so that the
+    // copy of one range overlaps the generation of the next
+    const int64_t per = std::max<int64_t>(1, std::min<int64_t>(st->count, kStage / row));
     void* stage[2] = {nullptr, nullptr};
     cudaStream_t cs = nullptr;
     cudaEvent_t done_gen[2], done_copy[2];
     CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     for (int i = 0; i < 2; ++i) {
-        CUDA_TRY(cudaMalloc(&stage[i], static_cast<size_t>(chunk * st->count * eb)));
+        CUDA_TRY(cudaMallocAsync(&stage[i], static_cast<size_t>(per * row), s));
         CUDA_TRY(cudaEventCreateWithFlags(&done_gen[i], cudaEventDisableTiming));
         CUDA_TRY(cudaEventCreateWithFlags(&done_copy[i], cudaEventDisableTiming));
         CUDA_TRY(cudaEventRecord(done_copy[i], cs));
     }
     int rc = VMT_OK;
-    int64_t off = 0;
-    for (int k = 0; off < n && rc == VMT_OK; ++k) {
+    int k = 0;
+    for (int64_t g0 = 0; g0 < st->count && rc == VMT_OK; g0 += per, ++k) {
         const int b = k & 1;
-        const int64_t m = std::min(chunk, n - off);
+        const int64_t gens = std::min(per, st->count - g0);
         CUDA_TRY(cudaStreamWaitEvent(s, done_copy[b], 0));
-        rc = vmt_generate(st, m, dtype, stage[b], s);
+        void* outs[1] = {stage[b]};
+        rc = generate_range(st, g0, gens, 1, &n, &dtype, outs, s);
         if (rc) break;
         CUDA_TRY(cudaEventRecord(done_gen[b], s));
         CUDA_TRY(cudaStreamWaitEvent(cs, done_gen[b], 0));
-        CUDA_TRY(cudaMemcpy2DAsync(static_cast<char*>(out_host) + off * eb, static_cast<size_t>(n * eb), stage[b],
-                                   static_cast<size_t>(m * eb), static_cast<size_t>(m * eb),
-                                   static_cast<size_t>(st->count), cudaMemcpyDeviceToHost, cs));
+        CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(out_host) + g0 * row, stage[b], static_cast<size_t>(gens * row),
+                                 cudaMemcpyDeviceToHost, cs));
         CUDA_TRY(cudaEventRecord(done_copy[b], cs));
-        off += m;
     }
     CUDA_TRY(cudaStreamSynchronize(cs));
-    CUDA_TRY(cudaStreamSynchronize(s));
     for (int i = 0; i < 2; ++i) {
-        cudaFree(stage[i]);
+        cudaFreeAsync(stage[i], s);
         cudaEventDestroy(done_gen[i]);
         cudaEventDestroy(done_copy[i]);
     }
+    CUDA_TRY(cudaStreamSynchronize(s));
     cudaStreamDestroy(cs);
+    if (rc == VMT_OK) st->block_pos = new_block_pos(vmt::block_words(st->variant, st->lanes), st->block_pos, n * words_per_output(st->variant, dtype));
     return rc;
 }
 
