@@ -151,6 +151,14 @@ int vmt_state_info(const vmt_state* st, int* variant, int* lanes, int64_t* count
 /* Device pointer of the combined states ([count][n][M] units) -- for tests. */
 void* vmt_state_device_ptr(const vmt_state* st);
 
+/*
+ * vmt_device_status -- VMT_ETIMEOUT if, since the last reset, a generation
+ * kernel gave up a bounded wait for one of its bulk copies (it then stops
+ * without writing its outputs), VMT_OK otherwise.  Synchronises the device's
+ * legacy stream.  reset != 0 clears the flag.
+ */
+int vmt_device_status(int reset);
+
 /* Release a state object (NULL is allowed). */
 void vmt_free(vmt_state* st);
 

@@ -23,7 +23,7 @@ LIB = os.path.join(OUT, "libvmt.so")
 
 CUDA_SOURCES = ["gen_mt.cu", "gen_sfmt.cu", "jump.cu", "vmt_capi.cu", "noalloc.cu"]
 CXX_SOURCES = ["gf2poly.cpp"]
-HEADERS = ["vmt_device.cuh", "vmt_internal.hpp", "gf2poly.hpp"]
+HEADERS = ["vmt_device.cuh", "vmt_internal.hpp", "gf2poly.hpp", "bulk.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -14,6 +14,7 @@
 // are independent (MT19937-32: 227/227/170 rows, MT19937-64: 156/156 rows).
 // Within a phase, row k also reads the old x_{k+1} that row k+1 overwrites, so
 // each phase loads all operands, synchronises, then writes.
+#include "bulk.cuh"
 #include "vmt_device.cuh"
 
 namespace vmt {
@@ -350,32 +351,55 @@ __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G
     }
 }
 
+// set by a kernel whose bounded wait on a bulk copy gave up
+__device__ int g_gen_timeout = 0;
+
 template <class G, int M, int VW, int T, class P>
 __global__ void __launch_bounds__(T) gen_mt_kernel(GenArgs a)
 {
     using W = typename G::W;
     constexpr int N = G::N, MM = G::MM, NM = N - MM;
     constexpr int B = N * M;        // words per block
-    constexpr int NV = B / VW;      // vectors per block
+    constexpr uint32_t BYTES = static_cast<uint32_t>(B * sizeof(W));
     static_assert(N <= 3 * NM, "at most three phases");
+    static_assert(BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
     // two copies of X-hat: the old block is only read while the new one is
-    // written, so a phase needs no barrier between its loads and its stores
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    W* const buf0 = reinterpret_cast<W*>(smem_raw);
-    W* const buf1 = buf0 + B;
+    // written, so a phase needs no barrier between its loads and its stores.
+    // A generator's state arrives and leaves with one bulk copy each; the
+    // next generator's state is fetched into the idle copy while the finished
+    // one is written back.
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    W* const bufs[2] = {reinterpret_cast<W*>(smem_raw), reinterpret_cast<W*>(smem_raw) + B};
+    __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x;
     using Plan = typename PlanOf<P>::type;
 
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    int cb = 0;   // copy that holds the current state
+    if (tid == 0 && blockIdx.x < a.gens) {
+        mbar_arrive_expect_tx(&bar, BYTES);
+        bulk_load(bufs[0], reinterpret_cast<const W*>(a.states) + blockIdx.x * static_cast<long long>(B), BYTES, &bar);
+    }
+
     for (long long gi = blockIdx.x; gi < a.gens; gi += gridDim.x) {
         W* gst = reinterpret_cast<W*>(a.states) + gi * static_cast<long long>(B);
-        W* cur = buf0;
-        W* nxt = buf1;
-        for (int v = tid; v < NV; v += T) {
-            W w[VW];
-            ldv<W, VW>(gst + v * VW, w);
-            stv<W, VW>(cur + v * VW, w);
+        const bool arrived = mbar_wait(&bar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(!arrived)) {
+            if (tid == 0) {
+                atomicExch(&g_gen_timeout, 1);
+                (void)mbar_wait(&bar, parity ^ 1u);   // give the late copy one more bounded chance
+                bulk_wait_all();
+            }
+            return;
         }
-        __syncthreads();
+        W* cur = bufs[cb];
+        W* nxt = bufs[cb ^ 1];
         const long long g = a.gen0 + gi;
         const Emitter em{a, g};
         const int total = static_cast<int>(a.total);
@@ -412,15 +436,26 @@ __global__ void __launch_bounds__(T) gen_mt_kernel(GenArgs a)
             W* t = cur;
             cur = nxt;
             nxt = t;
+            cb ^= 1;
             e += hi;
         }
-        for (int v = tid; v < NV; v += T) {
-            W w[VW];
-            ldv<W, VW>(cur + v * VW, w);
-            stv<W, VW>(gst + v * VW, w);
+        // write the state back and fetch the next generator's into the idle copy
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            bulk_store(gst, cur, BYTES);
+            bulk_commit();
+            const long long gj = gi + gridDim.x;
+            if (gj < a.gens) {
+                mbar_arrive_expect_tx(&bar, BYTES);
+                bulk_load(nxt, reinterpret_cast<const W*>(a.states) + gj * static_cast<long long>(B), BYTES, &bar);
+            }
+            bulk_wait_read();   // `cur` may be overwritten once the store has read it
         }
+        cb ^= 1;
         __syncthreads();
     }
+    if (tid == 0) bulk_wait_all();
 }
 
 template <class G, int M, int VW, int T, class P>
@@ -463,6 +498,18 @@ static cudaError_t launch_mt(const GenArgs& a, cudaStream_t st)
 }
 
 }  // namespace dev
+
+// 1 if a generation kernel gave up on a bounded wait since the last reset
+int read_generate_timeout(bool reset)
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, dev::g_gen_timeout, sizeof(int)) != cudaSuccess) return -1;
+    if (reset && v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(dev::g_gen_timeout, &z, sizeof(int));
+    }
+    return v;
+}
 
 cudaError_t launch_generate_mt(int variant, int lanes, const GenArgs& a, cudaStream_t s)
 {

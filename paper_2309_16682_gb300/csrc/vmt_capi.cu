@@ -808,6 +808,14 @@ int vmt_state_info(const vmt_state* st, int* variant, int* lanes, int64_t* count
 
 void* vmt_state_device_ptr(const vmt_state* st) { return st ? st->d_states : nullptr; }
 
+int vmt_device_status(int reset)
+{
+    const int v = vmt::read_generate_timeout(reset != 0);
+    if (v < 0) return fail(VMT_ECUDA, "could not read the device status flag");
+    if (v) return fail(VMT_ETIMEOUT, "a generation kernel gave up waiting for a bulk copy");
+    return VMT_OK;
+}
+
 void vmt_free(vmt_state* st)
 {
     if (!st) return;

@@ -58,6 +58,9 @@ cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, cudaStream
 cudaError_t launch_seed(int variant, long long count, const unsigned long long* seeds, void* base, cudaStream_t s);
 cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s);
 
+// 1 if a generation kernel gave up on a bounded wait (and reset the flag when asked)
+int read_generate_timeout(bool reset);
+
 // message returned by vmt_last_error() on this thread
 void set_last_error(const char* msg);
 
