@@ -38,6 +38,24 @@ METRIC = "random GB/s written (bit-exact)"
 UNIT = "GB/s"
 
 
+def profiled_traffic(key: str):
+    """DRAM bytes per launch of a kernel from profiles/traffic.json (an ncu
+    capture), or None when the kernel's sources changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)[key]
+        h = hashlib.sha256()
+        for src in t["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest()[:16] != t["source_sha"]:
+            return None
+        return float(t["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -228,6 +246,13 @@ def run_gb300(args, world, rank, local):
     unit_bytes = {"mt32": 4, "mt64": 8, "sfmt": 16}[w["variant"]]
     state_bytes = count * w["lanes"] * UNITS[vmt.VARIANTS[w["variant"]]] * unit_bytes
     outs = [torch.empty((count, n), dtype=vmt._torch_dtype(dt), device="cuda") for n, dt in segs]
+    tuned = None
+    if args.tune:
+        # the autotuner times each compiled CTA size on a slice of this workload
+        n_tune = sum(n for n, _ in segs)
+        tuned = vmt.autotune(w["variant"], w["lanes"], min(count, 16384), n_tune, segs[0][1], reps=3)
+    tune_threads = vmt.tune_get(w["variant"], w["lanes"])
+    traffic_key = ("gen_sfmt_kernel" if w["variant"] == "sfmt" else "gen_mt_kernel") + f"<{w['variant']}, M={w['lanes']}>"
 
     def step():
         g.generate_multi(segs, outs=outs)
@@ -297,12 +322,16 @@ def run_gb300(args, world, rank, local):
                        "l2": "no flush: each step writes %.1f GiB (> 129 MB L2)" % (out_bytes / 2**30),
                        "parallelism": f"{world} independent GPU(s), generators sharded, no collective"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (profiled_traffic(traffic_key) * count / w["generators"]
+                                     if profiled_traffic(traffic_key) is not None else None),
                          "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "output_only_frac": out_bytes / (launch_ms / 1e3) / 1e9 / peak,
-                         "kernel": "gen_mt_kernel<MT32,16,4,512>"},
+                         "kernel": ("gen_sfmt_kernel" if w["variant"] == "sfmt" else "gen_mt_kernel") +
+                                   f"<{w['variant']}, M={w['lanes']}>"},
             "gpu_launches": args.steps,
+            "tuning": {"threads": tune_threads, "autotune": tuned},
             "e2e": e2e,
             "cpu_baseline": cpu,
             "init": {"seconds": init_s, "lane_jumps": lane_jumps, "lane_jumps_per_s": lane_jumps / init_s,
@@ -321,6 +350,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="vmt32_m16_g65536", choices=sorted(I.WORKLOADS))
     ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--tune", action="store_true", help="run the autotuner before timing")
     ap.add_argument("--generators", type=int, default=0,
                     help="smaller generator count (profiling cases); default: the workload's")
     ap.add_argument("--no-e2e", action="store_true")

@@ -159,6 +159,20 @@ void* vmt_state_device_ptr(const vmt_state* st);
  */
 int vmt_device_status(int reset);
 
+/*
+ * Tuning of the generation kernels (the paper has no counterpart: CTA size is
+ * a GPU-specific choice).  Each (variant, lanes) pair has a small set of
+ * compiled CTA sizes; the table starts at the defaults, can be preset with the
+ * environment variable VMT_TUNE="mt32:16:1024,mt64:8:512", set directly, or
+ * filled by vmt_autotune, which times every compiled size on `count`
+ * generators producing n_per_gen outputs of `dtype` (reps timed calls each,
+ * after one warm-up) and keeps the fastest.  threads = 0 means the default.
+ */
+int vmt_tune_set(int variant, int lanes, int threads);
+int vmt_tune_get(int variant, int lanes);
+int vmt_autotune(int variant, int lanes, int64_t count, int64_t n_per_gen, int dtype, int reps, void* cuda_stream,
+                 int* best_threads, double* best_ms);
+
 /* Release a state object (NULL is allowed). */
 void vmt_free(vmt_state* st);
 

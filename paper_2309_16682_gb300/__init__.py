@@ -68,6 +68,10 @@ def lib() -> ctypes.CDLL:
             "vmt_poly_minpoly": (I, [P, I64, P, I64]),
             "vmt_poly_mulmod": (I, [P, P, P, P, I64]),
             "vmt_poly_x2pow": (I, [P, I64, I, I, P]),
+            "vmt_device_status": (I, [I]),
+            "vmt_tune_set": (I, [I, I, I]),
+            "vmt_tune_get": (I, [I, I]),
+            "vmt_autotune": (I, [I, I, I64, I64, I, I, P, P, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -189,6 +193,28 @@ class VGenerator:
             self.close()
         except Exception:
             pass
+
+
+def device_status(reset: bool = False) -> int:
+    """0, or raises VMTError(VMT_ETIMEOUT) if a kernel gave up a bounded wait."""
+    return _check(lib().vmt_device_status(1 if reset else 0))
+
+
+def tune_set(variant: str, lanes: int, threads: int) -> None:
+    _check(lib().vmt_tune_set(VARIANTS[variant], int(lanes), int(threads)))
+
+
+def tune_get(variant: str, lanes: int) -> int:
+    return _check(lib().vmt_tune_get(VARIANTS[variant], int(lanes)))
+
+
+def autotune(variant: str, lanes: int, count: int, n_per_gen: int, dtype: str = "u32", reps: int = 3, stream=None):
+    """Time every compiled CTA size and keep the fastest; returns (threads, ms per call)."""
+    t = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().vmt_autotune(VARIANTS[variant], int(lanes), int(count), int(n_per_gen), DTYPES[dtype], int(reps),
+                              _stream_handle(stream), ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
 
 
 def jump_poly(variant: str, d: int, log2_extra: int = 0) -> np.ndarray:

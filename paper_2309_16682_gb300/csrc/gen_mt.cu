@@ -312,38 +312,67 @@ __device__ __forceinline__ void emit_p(const typename PlanOf<P>::type& plan, con
     }
 }
 
-// One phase of the block twist: rows [K0, K1), reading the old block `cur`
-// and the rows of `nxt` finished by earlier phases.
+// One item of a twist phase: vector v of the new block from the old block
+// `cur` and the rows of `nxt` finished by earlier phases.
+template <class G, int M, int VW, int K0, int K1>
+__device__ __forceinline__ void twist_item(const typename G::W* cur, typename G::W* nxt, int v,
+                                           typename G::W (&z)[VW])
+{
+    using W = typename G::W;
+    constexpr int N = G::N, MM = G::MM, NM = N - MM;
+    constexpr int RV = M / VW, NV = N * RV;
+    W xa[VW], xb[VW], xc[VW], nw[VW];
+    ldv<W, VW>(cur + v * VW, xa);
+    if (K1 < N || v + RV < NV) ldv<W, VW>(cur + (v + RV) * VW, xb);   // old x_{k+1}
+    else ldv<W, VW>(nxt + (v + RV - NV) * VW, xb);                    // new x_0 for the last row
+    if (K0 == 0) ldv<W, VW>(cur + (v + MM * RV) * VW, xc);          // old x_{k+m}
+    else ldv<W, VW>(nxt + (v - NM * RV) * VW, xc);                  // new x_{k-(n-m)}
+#pragma unroll
+    for (int u = 0; u < VW; ++u) {
+        nw[u] = G::twist(xa[u], xb[u], xc[u]);
+        z[u] = G::temper(nw[u]);
+    }
+    stv<W, VW>(nxt + v * VW, nw);
+}
+
+// One phase of the block twist: rows [K0, K1).  When the whole phase is
+// emitted into one statically typed segment (the common case) the items run
+// without any per-vector check; otherwise every vector is routed by emit_p.
 template <class G, int M, int VW, int T, class P, int K0, int K1>
 __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G::W* nxt,
                                             const typename PlanOf<P>::type& plan, const Emitter& em, int hi,
                                             long long e, bool check)
 {
     using W = typename G::W;
-    constexpr int N = G::N, MM = G::MM, NM = N - MM;
-    constexpr int RV = M / VW, NV = N * RV;
+    constexpr int RV = M / VW;
     constexpr int V0 = K0 * RV, V1 = K1 * RV;
     constexpr int ITEMS = (V1 - V0 + T - 1) / T;
     const int tid = threadIdx.x;
+    if constexpr (!P::generic) {
+        const bool inside = !check || V1 * VW <= hi;   // every vector of the phase is emitted
+        if (inside && plan.ok && (P::nseg == 1 || plan.b1 >= V1 * VW || plan.b1 <= V0 * VW)) {
+            const bool second = P::nseg == 2 && plan.b1 <= V0 * VW;
+            const long long base = second ? plan.base1 : plan.base0;
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const int v = V0 + tid + i * T;
+                if (((i + 1) * T <= V1 - V0) || v < V1) {
+                    W z[VW];
+                    twist_item<G, M, VW, K0, K1>(cur, nxt, v, z);
+                    if (P::nseg == 2 && second) store_typed<(P::nseg == 2 ? P::DT1 : P::DT0), W, VW>(base, v * VW, z);
+                    else store_typed<P::DT0, W, VW>(base, v * VW, z);
+                }
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const int v = V0 + tid + i * T;
         const bool act = ((i + 1) * T <= V1 - V0) || v < V1;   // static for all but the last item
-        W nw[VW], z[VW];
-        if (act) {
-            W xa[VW], xb[VW], xc[VW];
-            ldv<W, VW>(cur + v * VW, xa);
-            if (K1 < N || v + RV < NV) ldv<W, VW>(cur + (v + RV) * VW, xb);   // old x_{k+1}
-            else ldv<W, VW>(nxt + (v + RV - NV) * VW, xb);                    // new x_0 for the last row
-            if (K0 == 0) ldv<W, VW>(cur + (v + MM * RV) * VW, xc);          // old x_{k+m}
-            else ldv<W, VW>(nxt + (v - NM * RV) * VW, xc);                  // new x_{k-(n-m)}
-#pragma unroll
-            for (int u = 0; u < VW; ++u) {
-                nw[u] = G::twist(xa[u], xb[u], xc[u]);
-                z[u] = G::temper(nw[u]);
-            }
-            stv<W, VW>(nxt + v * VW, nw);
-        } else {
+        W z[VW];
+        if (act) twist_item<G, M, VW, K0, K1>(cur, nxt, v, z);
+        else {
 #pragma unroll
             for (int u = 0; u < VW; ++u) z[u] = W(0);
         }
@@ -354,8 +383,20 @@ __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G
 // set by a kernel whose bounded wait on a bulk copy gave up
 __device__ int g_gen_timeout = 0;
 
+// CTAs that fit on one SM: by threads (2048) and by shared memory (two copies
+// of X-hat per CTA out of 227 KiB); the register budget follows from it.
+template <class G, int M, int T>
+constexpr int mt_ctas_per_sm()
+{
+    constexpr int by_threads = 2048 / T;
+    constexpr int by_smem = (227 * 1024) / (2 * G::N * M * static_cast<int>(sizeof(typename G::W)) + 1024);
+    constexpr int c = by_threads < by_smem ? by_threads : by_smem;
+    // with four or more CTAs one is traded for registers (no spills)
+    return c < 1 ? 1 : (c >= 4 ? c - 1 : c);
+}
+
 template <class G, int M, int VW, int T, class P>
-__global__ void __launch_bounds__(T) gen_mt_kernel(GenArgs a)
+__global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(GenArgs a)
 {
     using W = typename G::W;
     constexpr int N = G::N, MM = G::MM, NM = N - MM;
@@ -369,7 +410,7 @@ __global__ void __launch_bounds__(T) gen_mt_kernel(GenArgs a)
     // next generator's state is fetched into the idle copy while the finished
     // one is written back.
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    W* const bufs[2] = {reinterpret_cast<W*>(smem_raw), reinterpret_cast<W*>(smem_raw) + B};
+    W* const buf0 = reinterpret_cast<W*>(smem_raw);
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x;
     using Plan = typename PlanOf<P>::type;
@@ -383,7 +424,7 @@ __global__ void __launch_bounds__(T) gen_mt_kernel(GenArgs a)
     int cb = 0;   // copy that holds the current state
     if (tid == 0 && blockIdx.x < a.gens) {
         mbar_arrive_expect_tx(&bar, BYTES);
-        bulk_load(bufs[0], reinterpret_cast<const W*>(a.states) + blockIdx.x * static_cast<long long>(B), BYTES, &bar);
+        bulk_load(buf0, reinterpret_cast<const W*>(a.states) + blockIdx.x * static_cast<long long>(B), BYTES, &bar);
     }
 
     for (long long gi = blockIdx.x; gi < a.gens; gi += gridDim.x) {
@@ -398,8 +439,8 @@ __global__ void __launch_bounds__(T) gen_mt_kernel(GenArgs a)
             }
             return;
         }
-        W* cur = bufs[cb];
-        W* nxt = bufs[cb ^ 1];
+        W* cur = buf0 + cb * B;
+        W* nxt = buf0 + (cb ^ 1) * B;
         const long long g = a.gen0 + gi;
         const Emitter em{a, g};
         const int total = static_cast<int>(a.total);
@@ -514,21 +555,23 @@ int read_generate_timeout(bool reset)
 cudaError_t launch_generate_mt(int variant, int lanes, const GenArgs& a, cudaStream_t s)
 {
     using namespace dev;
+    // a.threads selects among the compiled CTA sizes (0: default)
+    const int t = a.threads;
     if (variant == VMT_MT19937_32) {
         switch (lanes) {
         case 1: return launch_mt<MT32, 1, 1, 256>(a, s);
         case 2: return launch_mt<MT32, 2, 2, 256>(a, s);
         case 4: return launch_mt<MT32, 4, 4, 256>(a, s);
-        case 8: return launch_mt<MT32, 8, 4, 256>(a, s);
-        case 16: return launch_mt<MT32, 16, 4, 512>(a, s);
+        case 8: return t == 512 ? launch_mt<MT32, 8, 4, 512>(a, s) : launch_mt<MT32, 8, 4, 256>(a, s);
+        case 16: return t == 1024 ? launch_mt<MT32, 16, 4, 1024>(a, s) : launch_mt<MT32, 16, 4, 512>(a, s);
         }
     } else if (variant == VMT_MT19937_64) {
         switch (lanes) {
         case 1: return launch_mt<MT64, 1, 1, 256>(a, s);
         case 2: return launch_mt<MT64, 2, 2, 256>(a, s);
         case 4: return launch_mt<MT64, 4, 2, 256>(a, s);
-        case 8: return launch_mt<MT64, 8, 2, 256>(a, s);
-        case 16: return launch_mt<MT64, 16, 2, 512>(a, s);
+        case 8: return t == 512 ? launch_mt<MT64, 8, 2, 512>(a, s) : launch_mt<MT64, 8, 2, 256>(a, s);
+        case 16: return t == 1024 ? launch_mt<MT64, 16, 2, 1024>(a, s) : launch_mt<MT64, 16, 2, 512>(a, s);
         }
     }
     return cudaErrorInvalidValue;

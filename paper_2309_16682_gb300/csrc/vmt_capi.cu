@@ -42,6 +42,59 @@ thread_local std::string g_err;
 
 void vmt::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
+// ---------------------------------------------------------------------------
+// tuning table: CTA size of the generation kernels per (variant, lanes)
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_lock;
+int g_tune_threads[3][17] = {};
+bool g_tune_env_read = false;
+
+// the CTA sizes compiled for each (variant, lanes); the first is the default
+std::vector<int> tune_candidates(int variant, int lanes)
+{
+    if (variant == VMT_SFMT19937) return {};
+    if (lanes == 8) return {256, 512};
+    if (lanes == 16) return {512, 1024};
+    return {};
+}
+
+void read_tune_env_locked()
+{
+    if (g_tune_env_read) return;
+    g_tune_env_read = true;
+    // VMT_TUNE="mt32:16:1024,mt64:8:512"
+    const char* e = std::getenv("VMT_TUNE");
+    if (!e) return;
+    std::string s(e);
+    size_t i = 0;
+    while (i < s.size()) {
+        size_t j = s.find(',', i);
+        if (j == std::string::npos) j = s.size();
+        const std::string item = s.substr(i, j - i);
+        int lanes = 0, threads = 0;
+        char name[8] = {0};
+        if (std::sscanf(item.c_str(), "%7[a-z0-9]:%d:%d", name, &lanes, &threads) == 3 && lanes >= 0 && lanes <= 16) {
+            const std::string n(name);
+            const int v = n == "mt32" ? 0 : (n == "mt64" ? 1 : (n == "sfmt" ? 2 : -1));
+            if (v >= 0) {
+                const auto c = tune_candidates(v, lanes);
+                if (std::find(c.begin(), c.end(), threads) != c.end()) g_tune_threads[v][lanes] = threads;
+            }
+        }
+        i = j + 1;
+    }
+}
+}  // namespace
+
+int vmt::tuned_threads(int variant, int lanes)
+{
+    if (variant < 0 || variant > 2 || lanes < 0 || lanes > 16) return 0;
+    std::lock_guard<std::mutex> lk(g_tune_lock);
+    read_tune_env_locked();
+    return g_tune_threads[variant][lanes];
+}
+
 namespace {
 
 int fail(int code, const std::string& msg)
@@ -404,6 +457,7 @@ int generate_range(vmt_state* st, int64_t g0, int64_t gens, int nseg, const int6
     a.states = static_cast<char*>(st->d_states) + g0 * vmt::state_bytes_per_gen(v, st->lanes);
     a.gens = gens;
     a.gen0 = 0;
+    a.threads = vmt::tuned_threads(v, st->lanes);
     a.pos = static_cast<int>(st->block_pos);
     a.nseg = nseg;
     int64_t w = 0;
@@ -821,6 +875,81 @@ void vmt_free(vmt_state* st)
     if (!st) return;
     if (st->d_states) cudaFree(st->d_states);
     delete st;
+}
+
+int vmt_tune_set(int variant, int lanes, int threads)
+{
+    if (!valid_variant(variant) || !valid_lanes(lanes)) return fail(VMT_EINVAL, "bad variant or lanes");
+    const auto c = tune_candidates(variant, lanes);
+    if (threads != 0 && std::find(c.begin(), c.end(), threads) == c.end())
+        return fail(VMT_EINVAL, "no kernel compiled with that CTA size for this variant and lane count");
+    std::lock_guard<std::mutex> lk(g_tune_lock);
+    read_tune_env_locked();
+    g_tune_threads[variant][lanes] = threads;
+    return VMT_OK;
+}
+
+int vmt_tune_get(int variant, int lanes)
+{
+    if (!valid_variant(variant) || !valid_lanes(lanes)) return fail(VMT_EINVAL, "bad variant or lanes");
+    return vmt::tuned_threads(variant, lanes);
+}
+
+int vmt_autotune(int variant, int lanes, int64_t count, int64_t n_per_gen, int dtype, int reps, void* cuda_stream,
+                 int* best_threads, double* best_ms)
+{
+    if (!valid_variant(variant) || !valid_lanes(lanes) || count < 1 || n_per_gen < 1 || reps < 1)
+        return fail(VMT_EINVAL, "bad autotune arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const auto cands = tune_candidates(variant, lanes);
+    std::vector<uint64_t> seeds(static_cast<size_t>(count));
+    for (int64_t g = 0; g < count; ++g) seeds[static_cast<size_t>(g)] = 0x9E3779B97F4A7C15ull * static_cast<uint64_t>(g + 1);
+    vmt_state* st = nullptr;
+    int rc = vmt_init_batch(&st, variant, lanes, count, seeds.data(), nullptr, cuda_stream);
+    if (rc) return rc;
+    void* out = nullptr;
+    const size_t bytes = static_cast<size_t>(count * n_per_gen * elem_bytes(dtype));
+    if (cudaMalloc(&out, bytes) != cudaSuccess) {
+        vmt_free(st);
+        return fail(VMT_ENOMEM, "autotune output buffer");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    double best_t = 1e30;
+    const std::vector<int> tried = cands.empty() ? std::vector<int>{0} : cands;
+    for (int threads : tried) {
+        {
+            std::lock_guard<std::mutex> lk(g_tune_lock);
+            g_tune_threads[variant][lanes] = threads;
+        }
+        rc = vmt_generate(st, n_per_gen, dtype, out, cuda_stream);   // warm-up
+        if (rc) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && rc == VMT_OK; ++r) rc = vmt_generate(st, n_per_gen, dtype, out, cuda_stream);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc) break;
+        if (ms / reps < best_t) {
+            best_t = ms / reps;
+            best = threads;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_lock);
+        g_tune_threads[variant][lanes] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    vmt_free(st);
+    if (rc) return rc;
+    if (best_threads) *best_threads = best;
+    if (best_ms) *best_ms = best_t;
+    return VMT_OK;
 }
 
 int vmt_poly_minpoly(const uint64_t* bits, int64_t n, uint64_t* mu_out, int64_t cap_words)

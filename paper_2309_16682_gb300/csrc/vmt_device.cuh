@@ -28,6 +28,27 @@ namespace dev {
 // ----------------------------------------------------------------------------
 // generator constants
 // ----------------------------------------------------------------------------
+// Exact right shift by s (0 < s < 32) as the high word of y * 2^(32-s): it
+// runs on the multiply-add pipe instead of the shift/logic pipe, which the XORs
+// of the tempering already keep busy.
+template <int S>
+__device__ __forceinline__ uint32_t shr_mulhi(uint32_t y)
+{
+    uint32_t r;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(r) : "r"(y), "r"(1u << (32 - S)));
+    return r;
+}
+
+// all ones when the lowest bit of x is set, else zero (x << 31, then the high
+// word of the signed product by 2), also on the multiply-add pipe
+__device__ __forceinline__ uint32_t low_bit_mask(uint32_t x)
+{
+    uint32_t t, r;
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(t) : "r"(x), "r"(0x80000000u));
+    asm("mul.hi.s32 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(2));
+    return r;
+}
+
 struct MT32 {
     using W = uint32_t;
     static constexpr int N = 624, MM = 397;
@@ -35,14 +56,14 @@ struct MT32 {
     {
         const W y = (xk & 0x80000000u) | (xk1 & 0x7FFFFFFFu);
         // y * A: y >> 1, XOR a when y is odd; y's lowest bit is xk1's lowest bit
-        return xkm ^ (y >> 1) ^ ((xk1 & 1u) * 0x9908B0DFu);
+        return xkm ^ shr_mulhi<1>(y) ^ (low_bit_mask(xk1) & 0x9908B0DFu);
     }
     static __device__ __forceinline__ W temper(W y)
     {
-        y ^= y >> 11;
+        y ^= shr_mulhi<11>(y);
         y ^= (y << 7) & 0x9D2C5680u;
         y ^= (y << 15) & 0xEFC60000u;
-        return y ^ (y >> 18);
+        return y ^ shr_mulhi<18>(y);
     }
 };
 

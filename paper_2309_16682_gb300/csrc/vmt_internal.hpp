@@ -38,6 +38,7 @@ struct GenArgs {
     long long total;   // native words per generator in this call
     int nseg;
     SegArg seg[VMT_MAXSEG];
+    int threads;       // CTA size among the compiled ones (0: default), set by the tuning table
 };
 
 // Jump work item: dst = c(F) src for one lane-state.  Unit u of the source
@@ -57,6 +58,9 @@ constexpr int kPolyWords = 640;  // u32 words per polynomial row (20480 bits)
 cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, cudaStream_t s);
 cudaError_t launch_seed(int variant, long long count, const unsigned long long* seeds, void* base, cudaStream_t s);
 cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s);
+
+// tuned CTA size for a (variant, lanes) pair (0: the kernel's default)
+int tuned_threads(int variant, int lanes);
 
 // 1 if a generation kernel gave up on a bounded wait (and reset the flag when asked)
 int read_generate_timeout(bool reset);

@@ -221,3 +221,22 @@ def test_full_workloads_sampled(vmt, oracle_polys, name):
             _assert_same(_np(outs[k][gi]), ref[k], f"{name} gen {gi} seg {k}")
     del outs
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("variant,M,threads", [("mt32", 16, 1024), ("mt32", 8, 512), ("mt64", 8, 512),
+                                               ("mt64", 16, 1024)])
+def test_every_cta_size_gives_the_same_stream(vmt, variant, M, threads):
+    seeds = I.splitmix64(77, 5)
+    native = "u64" if variant == "mt64" else "u32"
+    segs = [(3001, native), (9000, "f32"), (12345, native)]
+    prev = vmt.tune_get(variant, M)
+    try:
+        vmt.tune_set(variant, M, 0)
+        ref = [_np(t) for t in vmt.VGenerator(variant, M, seeds).generate_multi(segs)]
+        vmt.tune_set(variant, M, threads)
+        got = [_np(t) for t in vmt.VGenerator(variant, M, seeds).generate_multi(segs)]
+    finally:
+        vmt.tune_set(variant, M, prev)
+    for k in range(len(segs)):
+        assert np.array_equal(got[k], ref[k])
+    assert vmt.device_status() == 0
