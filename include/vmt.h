@@ -124,6 +124,37 @@ int vmt_generate_multi(vmt_state* st, int nseg, const int64_t* counts, const int
                        void* cuda_stream);
 
 /*
+ * vmt_generate_ragged -- generator g takes the next n[g] outputs of type dtype
+ * into the device buffer outs[g] (host arrays of count entries; n[g] may be 0).
+ * Generators then sit at different stream positions; later calls continue
+ * each one exactly.  All generators run in one persistent launch that hands
+ * them to CTAs longest first.  Limits: n[g] * words-per-output <= 2^30, and
+ * two-word outputs (u64/f64 from 32-bit generators) need an even stream
+ * position and at least 2 lanes (VMT_EINVAL otherwise).
+ */
+int vmt_generate_ragged(vmt_state* st, const int64_t* n, int dtype, void* const* outs, void* cuda_stream);
+
+/*
+ * Batches: many state objects (any variants and lane counts) generating in
+ * one pass.  vmt_batch_add(b, st, n, dtype, out) asks every generator g of st
+ * for its next n outputs at out + g*n; a state may appear once per batch.
+ * vmt_batch_run enqueues one persistent launch per (variant, lanes, dtype)
+ * group, units longest first; vmt_batch_run_graph does the same through a
+ * CUDA graph captured on its first call and replayed afterwards (the unit
+ * table, output pointers and lengths are fixed at capture; the stream
+ * positions advance on the device, so each replay continues every stream).
+ * Adding items or vmt_batch_clear drops the graph.  Same limits as
+ * vmt_generate_ragged.
+ */
+typedef struct vmt_batch vmt_batch;
+int vmt_batch_create(vmt_batch** b);
+int vmt_batch_add(vmt_batch* b, vmt_state* st, int64_t n, int dtype, void* out_dev);
+int vmt_batch_run(vmt_batch* b, void* cuda_stream);
+int vmt_batch_run_graph(vmt_batch* b, void* cuda_stream);
+int vmt_batch_clear(vmt_batch* b);
+void vmt_batch_destroy(vmt_batch* b);
+
+/*
  * vmt_generate_host -- as vmt_generate but into host memory (pinned or
  * pageable): the words are generated into a device staging buffer in chunks
  * and copied to out_host, generation of one chunk overlapping the copy of the
@@ -145,7 +176,7 @@ int64_t vmt_state_bytes(const vmt_state* st);
 int vmt_state_export(const vmt_state* st, void* host_buf, size_t cap, void* cuda_stream);
 int vmt_state_import(vmt_state* st, const void* host_buf, size_t len, void* cuda_stream);
 
-/* Variant, lanes M, generator count and current block position of a state. */
+/* Variant, lanes M, generator count and generator 0's current block position. */
 int vmt_state_info(const vmt_state* st, int* variant, int* lanes, int64_t* count, int64_t* block_pos);
 
 /* Device pointer of the combined states ([count][n][M] units) -- for tests. */

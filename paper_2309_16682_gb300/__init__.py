@@ -69,6 +69,13 @@ def lib() -> ctypes.CDLL:
             "vmt_poly_mulmod": (I, [P, P, P, P, I64]),
             "vmt_poly_x2pow": (I, [P, I64, I, I, P]),
             "vmt_device_status": (I, [I]),
+            "vmt_generate_ragged": (I, [P, P, I, P, P]),
+            "vmt_batch_create": (I, [PP]),
+            "vmt_batch_add": (I, [P, P, I64, I, P]),
+            "vmt_batch_run": (I, [P, P]),
+            "vmt_batch_run_graph": (I, [P, P]),
+            "vmt_batch_clear": (I, [P]),
+            "vmt_batch_destroy": (None, [P]),
             "vmt_tune_set": (I, [I, I, I]),
             "vmt_tune_get": (I, [I, I]),
             "vmt_autotune": (I, [I, I, I64, I64, I, I, P, P, P]),
@@ -152,6 +159,18 @@ class VGenerator:
         _check(lib().vmt_generate_host(self._h, int(n), DTYPES[dtype], ctypes.c_void_p(ptr), _stream_handle(stream)))
         return out
 
+    def generate_ragged(self, n, dtype: str = "u32", outs=None, stream=None):
+        """Generator g takes its next n[g] outputs; returns the list of tensors."""
+        import torch
+        n = [int(x) for x in n]
+        assert len(n) == self.count
+        if outs is None:
+            outs = [torch.empty(max(k, 1), dtype=_torch_dtype(dtype), device="cuda")[:k] for k in n]
+        na = np.ascontiguousarray(n, dtype=np.int64)
+        ptrs = (ctypes.c_void_p * self.count)(*[o.data_ptr() for o in outs])
+        _check(lib().vmt_generate_ragged(self._h, _np_ptr(na), DTYPES[dtype], ptrs, _stream_handle(stream)))
+        return outs
+
     # -- jump / state ---------------------------------------------------------
     def jump(self, poly: np.ndarray, nbits: int | None = None, stream=None):
         poly = np.ascontiguousarray(poly, dtype=np.uint64)
@@ -181,11 +200,44 @@ class VGenerator:
         hdr = 48
         buf = np.empty(n, np.uint8)
         _check(lib().vmt_state_export(self._h, _np_ptr(buf), n, _stream_handle(None)))
-        return buf[hdr:].reshape(self.count, -1)
+        return buf[hdr:n - 8 * self.count].reshape(self.count, -1)
 
     def close(self):
         if getattr(self, "_h", None):
             lib().vmt_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several generator sets produced in one pass (vmt_batch_*)."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib().vmt_batch_create(ctypes.byref(h)))
+        self._h = h
+        self._keep = []
+
+    def add(self, gen: VGenerator, n: int, dtype: str, out):
+        _check(lib().vmt_batch_add(self._h, gen._h, int(n), DTYPES[dtype], ctypes.c_void_p(out.data_ptr())))
+        self._keep.append((gen, out))
+
+    def run(self, stream=None, graph: bool = False):
+        f = lib().vmt_batch_run_graph if graph else lib().vmt_batch_run
+        _check(f(self._h, _stream_handle(stream)))
+
+    def clear(self):
+        _check(lib().vmt_batch_clear(self._h))
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vmt_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -79,7 +79,7 @@ struct BlockPlan {
     bool fast;   // every segment base aligned to a vector and every boundary on a vector
 
     template <class P, typename W, int VW>
-    __device__ __forceinline__ void make(const GenArgs& a, long long g, long long delta)
+    __device__ __forceinline__ void make(const GenArgs& a, const Emitter& em, long long delta)
     {
         const int lane = threadIdx.x & 31;
         int bnd = 0x7FFFFFFF;
@@ -91,7 +91,8 @@ struct BlockPlan {
             const int bpw = bytes_per_word<W>(sg.dtype);
             const int esz = (sg.dtype == VMT_U32 || sg.dtype == VMT_F32) ? 4 : 8;
             my_dt = sg.dtype;
-            my_base = reinterpret_cast<long long>(sg.out) + g * sg.count * esz + (delta - sg.wbeg) * bpw;
+            (void)esz;
+            my_base = reinterpret_cast<long long>(em.elem0(lane)) + (delta - sg.wbeg) * bpw;
             ok = (my_base % (VW * bpw)) == 0;
             long long b = sg.wbeg - delta;   // block word where the segment starts
             if (b < -1) b = -1;
@@ -257,18 +258,20 @@ struct TypedPlan {
     bool ok;
 
     template <class P, typename W, int VW>
-    __device__ __forceinline__ void make(const GenArgs& a, long long g, long long delta)
+    __device__ __forceinline__ void make(const GenArgs& a, const Emitter& em, long long delta)
     {
         const int bpw0 = bytes_per_word<W>(P::DT0);
         const int esz0 = (P::DT0 == VMT_U32 || P::DT0 == VMT_F32) ? 4 : 8;
-        base0 = reinterpret_cast<long long>(a.seg[0].out) + g * a.seg[0].count * esz0 + (delta - a.seg[0].wbeg) * bpw0;
+        (void)esz0;
+        base0 = reinterpret_cast<long long>(em.elem0(0)) + (delta - a.seg[0].wbeg) * bpw0;
         ok = (base0 % (VW * bpw0)) == 0;
         b1 = 0x7FFFFFFF;
         base1 = 0;
         if constexpr (P::nseg == 2) {
             const int bpw1 = bytes_per_word<W>(P::DT1);
             const int esz1 = (P::DT1 == VMT_U32 || P::DT1 == VMT_F32) ? 4 : 8;
-            base1 = reinterpret_cast<long long>(a.seg[1].out) + g * a.seg[1].count * esz1 + (delta - a.seg[1].wbeg) * bpw1;
+            (void)esz1;
+            base1 = reinterpret_cast<long long>(em.elem0(1)) + (delta - a.seg[1].wbeg) * bpw1;
             ok = ok && (base1 % (VW * bpw1)) == 0;
             long long b = a.seg[1].wbeg - delta;
             if (b < -1) b = -1;
@@ -395,7 +398,7 @@ constexpr int mt_ctas_per_sm()
     return c < 1 ? 1 : (c >= 4 ? c - 1 : c);
 }
 
-template <class G, int M, int VW, int T, class P>
+template <class G, int M, int VW, int T, class P, bool UNITS>
 __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(GenArgs a)
 {
     using W = typename G::W;
@@ -415,20 +418,41 @@ __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(
     const int tid = threadIdx.x;
     using Plan = typename PlanOf<P>::type;
 
+    __shared__ long long s_next;
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
-    __syncthreads();
+    // Generators (lock-step) or units (ragged / batched launches) are taken
+    // either in grid-stride order or, with a work counter, dynamically in the
+    // order of the unit list (longest first).  Thread 0 fetches the next one
+    // and starts the bulk copy of its state.
+    long long my_next = blockIdx.x;   // grid-stride cursor (thread 0)
+    auto take = [&]() -> long long {
+        if (UNITS && a.work_counter) return static_cast<long long>(atomicAdd(a.work_counter, 1));
+        const long long u = my_next;
+        my_next += gridDim.x;
+        return u;
+    };
+    auto state_of = [&](long long u) -> W* {
+        if constexpr (UNITS) return reinterpret_cast<W*>(a.units[u].state);
+        else return reinterpret_cast<W*>(a.states) + u * static_cast<long long>(B);
+    };
     uint32_t parity = 0;
     int cb = 0;   // copy that holds the current state
-    if (tid == 0 && blockIdx.x < a.gens) {
-        mbar_arrive_expect_tx(&bar, BYTES);
-        bulk_load(buf0, reinterpret_cast<const W*>(a.states) + blockIdx.x * static_cast<long long>(B), BYTES, &bar);
+    if (tid == 0) {
+        const long long u = take();
+        s_next = u;
+        if (u < a.gens) {
+            mbar_arrive_expect_tx(&bar, BYTES);
+            bulk_load(buf0, state_of(u), BYTES, &bar);
+        }
     }
+    __syncthreads();
+    long long gi = s_next;
 
-    for (long long gi = blockIdx.x; gi < a.gens; gi += gridDim.x) {
-        W* gst = reinterpret_cast<W*>(a.states) + gi * static_cast<long long>(B);
+    while (gi < a.gens) {
+        W* gst = state_of(gi);
         const bool arrived = mbar_wait(&bar, parity);
         parity ^= 1u;
         if (__syncthreads_or(!arrived)) {
@@ -441,16 +465,20 @@ __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(
         }
         W* cur = buf0 + cb * B;
         W* nxt = buf0 + (cb ^ 1) * B;
-        const long long g = a.gen0 + gi;
-        const Emitter em{a, g};
-        const int total = static_cast<int>(a.total);
+        // lock-step launches take position and length from the kernel
+        // parameters (uniform values); unit launches from the unit table
+        const UnitDesc* ud = UNITS ? &a.units[gi] : nullptr;
+        const Emitter em{a, a.gen0 + gi, UNITS ? ud->out : nullptr};
+        int* posp = UNITS ? ud->pos : a.pos_dev + gi;
+        const int total = static_cast<int>(UNITS ? ud->total : a.total);
         int e = 0;
-        const int p = a.pos;
+        const int p = UNITS ? *posp : a.pos;
+        int final_pos = p;
         Plan plan;
         if (p < B && total > 0) {
             // rest of the current block: block word f is call word f - p
             const int hi = min(B, p + total);
-            plan.template make<P, W, VW>(a, g, -static_cast<long long>(p));
+            plan.template make<P, W, VW>(a, em, -static_cast<long long>(p));
             for (int v0 = p / VW; v0 * VW < hi; v0 += T) {
                 const int v = v0 + tid;
                 W w[VW], z[VW];
@@ -461,11 +489,12 @@ __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(
                 emit_p<P, W, VW>(plan, em, v * VW, z, p, hi, -static_cast<long long>(p), act, true);
             }
             e = hi - p;
+            final_pos = hi;
         }
         while (e < total) {
             const int hi = min(B, total - e);   // block words [0, hi) are emitted
             const bool check = hi < B;
-            plan.template make<P, W, VW>(a, g, e);
+            plan.template make<P, W, VW>(a, em, e);
             twist_phase<G, M, VW, T, P, 0, NM>(cur, nxt, plan, em, hi, e, check);
             __syncthreads();
             twist_phase<G, M, VW, T, P, NM, (2 * NM < N ? 2 * NM : N)>(cur, nxt, plan, em, hi, e, check);
@@ -479,40 +508,59 @@ __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(
             nxt = t;
             cb ^= 1;
             e += hi;
+            final_pos = hi;
         }
         // write the state back and fetch the next generator's into the idle copy
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
+            *posp = final_pos;
             bulk_store(gst, cur, BYTES);
             bulk_commit();
-            const long long gj = gi + gridDim.x;
+            const long long gj = take();
+            s_next = gj;
             if (gj < a.gens) {
                 mbar_arrive_expect_tx(&bar, BYTES);
-                bulk_load(nxt, reinterpret_cast<const W*>(a.states) + gj * static_cast<long long>(B), BYTES, &bar);
+                bulk_load(nxt, state_of(gj), BYTES, &bar);
             }
             bulk_wait_read();   // `cur` may be overwritten once the store has read it
         }
         cb ^= 1;
         __syncthreads();
+        gi = s_next;
     }
     if (tid == 0) bulk_wait_all();
+}
+
+template <class G, int M, int VW, int T, class P, bool UNITS>
+static cudaError_t launch_mt_pu(const GenArgs& a, cudaStream_t st)
+{
+    constexpr int smem = 2 * G::N * M * static_cast<int>(sizeof(typename G::W));
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(gen_mt_kernel<G, M, VW, T, P, UNITS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    // unit launches are persistent: a few CTAs per SM pull units from the counter
+    long long grid = a.gens < (1LL << 30) ? a.gens : (1LL << 30);
+    if (UNITS && a.work_counter) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long persistent = static_cast<long long>(sms) * mt_ctas_per_sm<G, M, T>();
+        if (grid > persistent) grid = persistent;
+    }
+    gen_mt_kernel<G, M, VW, T, P, UNITS><<<static_cast<unsigned>(grid), T, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 template <class G, int M, int VW, int T, class P>
 static cudaError_t launch_mt_p(const GenArgs& a, cudaStream_t st)
 {
-    constexpr int smem = 2 * G::N * M * static_cast<int>(sizeof(typename G::W));
-    static bool attr_set = false;
-    if (!attr_set) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(gen_mt_kernel<G, M, VW, T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const long long grid = a.gens < (1LL << 30) ? a.gens : (1LL << 30);
-    gen_mt_kernel<G, M, VW, T, P><<<static_cast<unsigned>(grid), T, smem, st>>>(a);
-    return cudaGetLastError();
+    if (a.units) return launch_mt_pu<G, M, VW, T, P, true>(a, st);
+    return launch_mt_pu<G, M, VW, T, P, false>(a, st);
 }
 
 // policy dispatch: typed kernels for the common type patterns, generic otherwise

@@ -238,9 +238,35 @@ template <class J> struct ApplyAll<J, J::R + 1> {
                                                const typename J::U (&)[J::R]) {}
 };
 
+// Work item `item` of a grid description (see JumpGrid); false when the item
+// has nothing to do (a zero digit).
+__device__ __forceinline__ bool grid_item(const JumpGrid& gr, long long item, JumpItem& it)
+{
+    if (gr.mode == JumpGrid::kFanOut) {
+        const long long g = item / gr.lanes;
+        const int t = static_cast<int>(item % gr.lanes);
+        it.src = gr.base + g * gr.unit_bytes;
+        it.src_stride = static_cast<int>(gr.count);
+        it.dst = gr.states + g * gr.gen_bytes + static_cast<long long>(t) * gr.unit_bytes;
+        it.dst_stride = gr.lanes;
+        it.poly = t * 16 / gr.lanes;
+    } else {
+        const long long g = item;
+        const int dig = static_cast<int>((gr.jumps[g] >> (8 * gr.digit)) & 255u);
+        if (dig == 0) return false;
+        it.src = gr.base + g * gr.unit_bytes;
+        it.dst = gr.base + g * gr.unit_bytes;
+        it.src_stride = static_cast<int>(gr.count);
+        it.dst_stride = static_cast<int>(gr.count);
+        it.poly = 16 + 255 * gr.digit + dig - 1;
+    }
+    it.deg = gr.row_deg[it.poly];
+    return true;
+}
+
 template <class J>
-__global__ void __launch_bounds__(kJumpWarps * 32) jump_kernel(const JumpItem* items, long long nitems,
-                                                                const uint32_t* polys)
+__global__ void __launch_bounds__(kJumpWarps * 32) jump_kernel(const JumpItem* items, JumpGrid grid,
+                                                                long long nitems, const uint32_t* polys)
 {
     using U = typename J::U;
     constexpr int N = J::N, R = J::R, RING = J::RING, C = J::C;
@@ -250,7 +276,9 @@ __global__ void __launch_bounds__(kJumpWarps * 32) jump_kernel(const JumpItem* i
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long item = static_cast<long long>(blockIdx.x) * kJumpWarps + warp;
     if (item >= nitems) return;  // whole warp leaves together
-    const JumpItem it = items[item];
+    JumpItem it;
+    if (items) it = items[item];
+    else if (!grid_item(grid, item, it)) return;
     U* ring = ring_all[warp];
     for (int u = lane; u < N; u += 32) ring[u] = ld_unit<U>(it.src, static_cast<long long>(u) * it.src_stride);
     __syncwarp();
@@ -290,12 +318,20 @@ __global__ void __launch_bounds__(kJumpWarps * 32) jump_kernel(const JumpItem* i
 }
 
 template <class J>
-static cudaError_t launch_jump_t(const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t st)
+static cudaError_t launch_jump_t(const JumpItem* items, const JumpGrid& gr, long long nitems, const uint32_t* polys,
+                                 cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
     const long long grid = (nitems + kJumpWarps - 1) / kJumpWarps;
-    jump_kernel<J><<<static_cast<unsigned>(grid), kJumpWarps * 32, 0, st>>>(items, nitems, polys);
+    jump_kernel<J><<<static_cast<unsigned>(grid), kJumpWarps * 32, 0, st>>>(items, gr, nitems, polys);
     return cudaGetLastError();
+}
+
+__global__ void fill_int_kernel(int* p, long long n, int v)
+{
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        p[i] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -345,9 +381,27 @@ cudaError_t launch_seed(int variant, long long count, const unsigned long long* 
 cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s)
 {
     using namespace dev;
-    if (variant == VMT_MT19937_32) return launch_jump_t<JMT32>(items, nitems, polys, s);
-    if (variant == VMT_MT19937_64) return launch_jump_t<JMT64>(items, nitems, polys, s);
-    return launch_jump_t<JSFMT>(items, nitems, polys, s);
+    const JumpGrid none{};
+    if (variant == VMT_MT19937_32) return launch_jump_t<JMT32>(items, none, nitems, polys, s);
+    if (variant == VMT_MT19937_64) return launch_jump_t<JMT64>(items, none, nitems, polys, s);
+    return launch_jump_t<JSFMT>(items, none, nitems, polys, s);
+}
+
+cudaError_t launch_jump_grid(int variant, const JumpGrid& gr, long long nitems, const uint32_t* polys, cudaStream_t s)
+{
+    using namespace dev;
+    if (variant == VMT_MT19937_32) return launch_jump_t<JMT32>(nullptr, gr, nitems, polys, s);
+    if (variant == VMT_MT19937_64) return launch_jump_t<JMT64>(nullptr, gr, nitems, polys, s);
+    return launch_jump_t<JSFMT>(nullptr, gr, nitems, polys, s);
+}
+
+cudaError_t launch_fill_int(int* p, long long n, int value, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long grid = (n + 255) / 256;
+    if (grid > 4096) grid = 4096;
+    dev::fill_int_kernel<<<static_cast<unsigned>(grid), 256, 0, s>>>(p, n, value);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_convert(const void* words, long long words_per_gen, int word64, long long gens, long long wbeg,

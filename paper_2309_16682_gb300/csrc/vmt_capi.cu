@@ -16,6 +16,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "gf2poly.hpp"
@@ -23,14 +24,14 @@
 
 namespace vmt {
 cudaError_t launch_generate_mt(int variant, int lanes, const GenArgs& a, cudaStream_t s);
-cudaError_t launch_generate_sfmt(int lanes, const GenArgs& a, cudaStream_t s);
+cudaError_t launch_generate_sfmt(int lanes, const GenArgs& a, bool ragged, cudaStream_t s);
 cudaError_t launch_convert(const void* words, long long words_per_gen, int word64, long long gens, long long wbeg,
                            int dtype, long long count, void* out, cudaStream_t s);
 
-cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, cudaStream_t s)
+cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, bool ragged, cudaStream_t s)
 {
-    if (variant == VMT_SFMT19937) return launch_generate_sfmt(lanes, a, s);
-    return launch_generate_mt(variant, lanes, a, s);
+    if (variant == VMT_SFMT19937) return launch_generate_sfmt(lanes, a, ragged, s);
+    return launch_generate_mt(variant, lanes, a, s);   // one CTA per generator: ragged needs nothing special
 }
 }  // namespace vmt
 
@@ -139,6 +140,7 @@ struct VariantCtx {
     int device = -1;
     uint32_t* d_table = nullptr;   // [16 + kDigitRows][kPolyWords]
     std::vector<int> row_deg;      // degree of each device row
+    int* d_row_deg = nullptr;      // the same, on the device
 };
 
 VariantCtx g_ctx[3];
@@ -238,11 +240,15 @@ int sample_bits(int variant, int bit, int64_t nbits, std::vector<uint64_t>& pack
     const unsigned long long seed = 5489ull;
     CUDA_TRY(cudaMemcpyAsync(d_seed, &seed, 8, cudaMemcpyHostToDevice, st));
     CUDA_TRY(vmt::launch_seed(variant, 1, d_seed, d_state, st));
+    int* d_pos1 = nullptr;
+    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_pos1), sizeof(int), st));
+    CUDA_TRY(vmt::launch_fill_int(d_pos1, 1, static_cast<int>(vmt::block_words(variant, 1)), st));
     vmt::GenArgs a{};
     a.states = d_state;
     a.gens = 1;
     a.gen0 = 0;
-    a.pos = static_cast<int>(vmt::block_words(variant, 1));
+    a.pos = static_cast<int>(vmt::block_words(variant, 1));   // fresh state: the first output twists
+    a.pos_dev = d_pos1;
     a.total = words;
     a.nseg = 1;
     a.seg[0].out = static_cast<char*>(d_out);
@@ -251,13 +257,14 @@ int sample_bits(int variant, int bit, int64_t nbits, std::vector<uint64_t>& pack
     a.seg[0].wend = words;
     a.seg[0].dtype = (variant == VMT_MT19937_64) ? VMT_U64 : VMT_U32;
     a.seg[0].fast = 0;
-    CUDA_TRY(vmt::launch_generate(variant, 1, a, st));
+    CUDA_TRY(vmt::launch_generate(variant, 1, a, false, st));
     std::vector<unsigned char> host(static_cast<size_t>(words * wb));
     CUDA_TRY(cudaMemcpyAsync(host.data(), d_out, words * wb, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     cudaFreeAsync(d_seed, st);
     cudaFreeAsync(d_state, st);
     cudaFreeAsync(d_out, st);
+    cudaFreeAsync(d_pos1, st);
     packed.assign(static_cast<size_t>((nbits + 63) / 64), 0);
     for (int64_t i = 0; i < nbits; ++i) {
         uint64_t v;
@@ -350,6 +357,10 @@ int ensure_variant(int variant, cudaStream_t st)
             c.row_deg[static_cast<size_t>(s)] = vmt::gf2::degree(c.lane_rows[static_cast<size_t>(s)]);
         }
         CUDA_TRY(cudaMemcpy(c.d_table, host.data(), host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        if (c.d_row_deg) cudaFree(c.d_row_deg);
+        c.d_row_deg = nullptr;
+        CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&c.d_row_deg), rows * sizeof(int)));
+        CUDA_TRY(cudaMemcpy(c.d_row_deg, c.row_deg.data(), rows * sizeof(int), cudaMemcpyHostToDevice));
         c.device = dev;
         c.digits_ready = false;
     }
@@ -382,6 +393,7 @@ int ensure_digits(int variant)
     }
     CUDA_TRY(cudaMemcpy(c.d_table + 16 * static_cast<size_t>(vmt::kPolyWords), host.data(),
                         host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c.d_row_deg, c.row_deg.data(), c.row_deg.size() * sizeof(int), cudaMemcpyHostToDevice));
     c.digits_ready = true;
     return VMT_OK;
 }
@@ -395,26 +407,26 @@ struct vmt_state {
     int variant = 0;
     int lanes = 0;
     int64_t count = 0;
-    int64_t block_pos = 0;     // native words of the current block already emitted
-    void* d_states = nullptr;  // [count][block words]
+    std::vector<int64_t> h_pos;  // per generator: native words of its current block already emitted
+    bool uniform = true;         // all h_pos equal
+    int* d_pos = nullptr;        // device copy, read and written by the generation kernels
+    void* d_states = nullptr;    // [count][block words]
     int device = 0;
+    // unit-launch scratch (ragged calls): pinned host staging and device copy
+    vmt::UnitDesc* h_units = nullptr;
+    vmt::UnitDesc* d_units = nullptr;
+    int* d_counter = nullptr;
+    int64_t units_cap = 0;
+    cudaEvent_t units_free = nullptr;   // recorded after the last upload of h_units
 };
 
 namespace {
 
 int64_t state_total_bytes(const vmt_state* st) { return st->count * vmt::state_bytes_per_gen(st->variant, st->lanes); }
 
-int run_jump_items(int variant, const std::vector<vmt::JumpItem>& items, const uint32_t* table, cudaStream_t s)
+int run_jump_grid(int variant, const vmt::JumpGrid& gr, long long nitems, const uint32_t* table, cudaStream_t s)
 {
-    if (items.empty()) return VMT_OK;
-    vmt::JumpItem* d_items = nullptr;
-    const size_t bytes = items.size() * sizeof(vmt::JumpItem);
-    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_items), bytes, s));
-    CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), bytes, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(vmt::launch_jump(variant, d_items, static_cast<long long>(items.size()), table, s));
-    CUDA_TRY(cudaFreeAsync(d_items, s));
-    // the items vector is host memory read by the async copy: keep it alive
-    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(vmt::launch_jump_grid(variant, gr, nitems, table, s));
     return VMT_OK;
 }
 
@@ -426,6 +438,35 @@ int64_t new_block_pos(int64_t B, int64_t p, int64_t total)
     if (rem == 0) return p + first;
     const int64_t nblocks = (rem + B - 1) / B;
     return rem - (nblocks - 1) * B;
+}
+
+// advance the host copy of the positions of generators [g0, g0+gens) by `words`
+void advance_positions(vmt_state* st, int64_t g0, int64_t gens, int64_t words)
+{
+    const int64_t B = vmt::block_words(st->variant, st->lanes);
+    for (int64_t g = g0; g < g0 + gens; ++g) st->h_pos[static_cast<size_t>(g)] = new_block_pos(B, st->h_pos[static_cast<size_t>(g)], words);
+}
+
+void refresh_uniform(vmt_state* st)
+{
+    st->uniform = true;
+    for (size_t g = 1; g < st->h_pos.size() && st->uniform; ++g) st->uniform = st->h_pos[g] == st->h_pos[0];
+}
+
+bool range_uniform(const vmt_state* st, int64_t g0, int64_t gens)
+{
+    if (st->uniform) return true;
+    for (int64_t g = g0 + 1; g < g0 + gens; ++g)
+        if (st->h_pos[static_cast<size_t>(g)] != st->h_pos[static_cast<size_t>(g0)]) return false;
+    return true;
+}
+
+bool any_odd(const vmt_state* st, int64_t g0, int64_t gens, int64_t w)
+{
+    if (st->uniform) return ((st->h_pos[0] + w) & 1) != 0;
+    for (int64_t g = g0; g < g0 + gens; ++g)
+        if (((st->h_pos[static_cast<size_t>(g)] + w) & 1) != 0) return true;
+    return false;
 }
 
 int words_per_output(int variant, int dtype)
@@ -443,6 +484,47 @@ int vector_width(int variant, int lanes)
     return std::min(lanes, 2);
 }
 
+constexpr int64_t kMaxUnitWords = int64_t(1) << 30;
+
+// grow a pinned host buffer and a device buffer of unit descriptors
+int reserve_units(vmt::UnitDesc** h, vmt::UnitDesc** d, int** counter, int64_t* cap, cudaEvent_t* free_ev,
+                  int64_t n)
+{
+    if (!*free_ev) CUDA_TRY(cudaEventCreateWithFlags(free_ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventSynchronize(*free_ev));   // the previous upload has been read
+    if (n > *cap) {
+        if (*h) cudaFreeHost(*h);
+        if (*d) cudaFree(*d);
+        *h = nullptr;
+        *d = nullptr;
+        const int64_t c = std::max<int64_t>(n, 64);
+        CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(h), static_cast<size_t>(c) * sizeof(vmt::UnitDesc), 0));
+        CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(d), static_cast<size_t>(c) * sizeof(vmt::UnitDesc)));
+        *cap = c;
+    }
+    if (!*counter) CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(counter), 16 * sizeof(int)));
+    return VMT_OK;
+}
+
+// one persistent unit launch: units already in d_units[0..n), counter slot k
+int launch_units(int variant, int lanes, int dtype, const vmt::UnitDesc* d_units, int64_t n, int* counter,
+                 cudaStream_t s)
+{
+    if (n == 0) return VMT_OK;
+    vmt::GenArgs a{};
+    a.gens = n;
+    a.threads = vmt::tuned_threads(variant, lanes);
+    a.nseg = 1;
+    a.seg[0].dtype = dtype;
+    a.seg[0].wbeg = 0;
+    a.seg[0].wend = kMaxUnitWords;
+    a.units = d_units;
+    a.work_counter = counter;
+    CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    CUDA_TRY(vmt::launch_generate(variant, lanes, a, true, s));
+    return VMT_OK;
+}
+
 // Generate `nseg` consecutive segments for generators [g0, g0 + gens) of st,
 // whose outputs start at outs[i] (generator g0 writes at outs[i] + 0).  The
 // block position is not advanced: all generator ranges of one call start at the
@@ -458,8 +540,10 @@ int generate_range(vmt_state* st, int64_t g0, int64_t gens, int nseg, const int6
     a.gens = gens;
     a.gen0 = 0;
     a.threads = vmt::tuned_threads(v, st->lanes);
-    a.pos = static_cast<int>(st->block_pos);
+    a.pos_dev = st->d_pos + g0;
+    a.pos = static_cast<int>(st->h_pos[static_cast<size_t>(g0)]);
     a.nseg = nseg;
+    const bool ragged = !range_uniform(st, g0, gens);
     int64_t w = 0;
     bool generic = false;
     for (int i = 0; i < nseg; ++i) {
@@ -480,24 +564,54 @@ int generate_range(vmt_state* st, int64_t g0, int64_t gens, int nseg, const int6
         if (wpo == 2 && counts[i] > 0) {
             // a pair must sit inside one thread's vector: even absolute start and
             // vectors of at least two words
-            if (((st->block_pos + w) & 1) != 0 || vector_width(v, st->lanes) < 2) generic = true;
+            if (any_odd(st, g0, gens, w) || vector_width(v, st->lanes) < 2) generic = true;
         }
         w += counts[i] * wpo;
     }
     a.total = w;
     if (w == 0 || gens == 0) return VMT_OK;
+    if (ragged) {
+        // generators at different positions: one unit launch per segment, each
+        // generator a unit of that segment's length (positions advance on the
+        // device from one segment to the next)
+        if (generic) return fail(VMT_EINVAL, "two-word outputs need even stream positions when generators differ");
+        int rc = reserve_units(&st->h_units, &st->d_units, &st->d_counter, &st->units_cap, &st->units_free, gens);
+        if (rc) return rc;
+        const int64_t gen_bytes = vmt::state_bytes_per_gen(v, st->lanes);
+        for (int i = 0; i < nseg; ++i) {
+            const vmt::SegArg& sg = a.seg[i];
+            const int64_t sw = sg.wend - sg.wbeg;
+            if (sw == 0) continue;
+            if (sw > kMaxUnitWords) return fail(VMT_EINVAL, "segment too long for generators at different positions");
+            CUDA_TRY(cudaEventSynchronize(st->units_free));
+            for (int64_t g = 0; g < gens; ++g) {
+                vmt::UnitDesc& u = st->h_units[g];
+                u.state = static_cast<char*>(st->d_states) + (g0 + g) * gen_bytes;
+                u.pos = st->d_pos + g0 + g;
+                u.total = sw;
+                u.out = sg.out + g * sg.count * elem_bytes(sg.dtype);
+            }
+            CUDA_TRY(cudaMemcpyAsync(st->d_units, st->h_units, static_cast<size_t>(gens) * sizeof(vmt::UnitDesc),
+                                     cudaMemcpyHostToDevice, s));
+            CUDA_TRY(cudaEventRecord(st->units_free, s));
+            rc = launch_units(v, st->lanes, sg.dtype, st->d_units, gens, st->d_counter, s);
+            if (rc) return rc;
+        }
+        return VMT_OK;
+    }
     // the kernels index words of one call with 32-bit integers: longer calls
     // are cut into pieces of at most 2^30 words (an even number, so that no
     // output pair is split); each piece starts where the previous one ended
     constexpr int64_t kPiece = int64_t(1) << 30;
     if (!generic && w > kPiece) {
+        int64_t pos = a.pos;
         const int64_t B = vmt::block_words(v, st->lanes);
-        int64_t pos = st->block_pos;
         for (int64_t w0 = 0; w0 < w; w0 += kPiece) {
             const int64_t w1 = std::min(w, w0 + kPiece);
             vmt::GenArgs pa = a;
             pa.pos = static_cast<int>(pos);
             pa.total = w1 - w0;
+            pos = new_block_pos(B, pos, w1 - w0);
             pa.nseg = 0;
             for (int i = 0; i < nseg; ++i) {
                 const vmt::SegArg& sg = a.seg[i];
@@ -512,15 +626,14 @@ int generate_range(vmt_state* st, int64_t g0, int64_t gens, int nseg, const int6
                 q.wend = hi - w0;
                 pa.seg[pa.nseg++] = q;
             }
-            CUDA_TRY(vmt::launch_generate(v, st->lanes, pa, s));
-            pos = new_block_pos(B, pos, w1 - w0);
+            CUDA_TRY(vmt::launch_generate(v, st->lanes, pa, ragged, s));
         }
         return VMT_OK;
     }
     if (generic && w > kPiece)
         return fail(VMT_EINVAL, "two-word outputs at an odd word offset are limited to 2^30 words per call");
     if (!generic) {
-        CUDA_TRY(vmt::launch_generate(v, st->lanes, a, s));
+        CUDA_TRY(vmt::launch_generate(v, st->lanes, a, ragged, s));
     } else {
         // raw native words into scratch, then one conversion per segment
         const int wb = vmt::word_bytes(v);
@@ -534,7 +647,7 @@ int generate_range(vmt_state* st, int64_t g0, int64_t gens, int nseg, const int6
         r.seg[0].wend = w;
         r.seg[0].dtype = (v == VMT_MT19937_64) ? VMT_U64 : VMT_U32;
         r.seg[0].fast = 0;
-        CUDA_TRY(vmt::launch_generate(v, st->lanes, r, s));
+        CUDA_TRY(vmt::launch_generate(v, st->lanes, r, ragged, s));
         for (int i = 0; i < nseg; ++i)
             CUDA_TRY(vmt::launch_convert(scratch, w, v == VMT_MT19937_64, gens, a.seg[i].wbeg, a.seg[i].dtype,
                                          a.seg[i].count, a.seg[i].out, s));
@@ -556,8 +669,7 @@ int generate_impl(vmt_state* st, int nseg, const int64_t* counts, const int* dty
     if (!st) return fail(VMT_EINVAL, "null state");
     const int rc = generate_range(st, 0, st->count, nseg, counts, dtypes, outs, s);
     if (rc) return rc;
-    st->block_pos = new_block_pos(vmt::block_words(st->variant, st->lanes), st->block_pos,
-                                  call_words(st, nseg, counts, dtypes));
+    advance_positions(st, 0, st->count, call_words(st, nseg, counts, dtypes));
     return VMT_OK;
 }
 
@@ -600,59 +712,54 @@ int vmt_init_batch(vmt_state** out, int variant, int lanes, int64_t count, const
     st->count = count;
     CUDA_TRY(cudaGetDevice(&st->device));
     const int64_t bytes = state_total_bytes(st.get());
-    if (cudaMalloc(&st->d_states, static_cast<size_t>(bytes)) != cudaSuccess) {
+    const int64_t B = vmt::block_words(variant, lanes);
+    if (cudaMalloc(&st->d_states, static_cast<size_t>(bytes)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&st->d_pos), static_cast<size_t>(count) * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
+        if (st->d_states) cudaFree(st->d_states);
         return fail(VMT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " state bytes failed");
     }
+    st->h_pos.assign(static_cast<size_t>(count), B);   // exhausted: the first output twists
+    st->uniform = true;
+    CUDA_TRY(vmt::launch_fill_int(st->d_pos, count, static_cast<int>(B), s));
     const int n_units = vmt::units_per_lane(variant);
-    const int64_t unit_bytes = static_cast<int64_t>(vmt::word_bytes(variant)) * vmt::words_per_unit(variant);
-    // scratch: seeds and the unjumped base states, unit-major [u][g]
+    const int unit_bytes = vmt::word_bytes(variant) * vmt::words_per_unit(variant);
+    // scratch: seeds, offsets and the unjumped base states, unit-major [u][g]
     unsigned long long* d_seeds = nullptr;
+    unsigned long long* d_jumps = nullptr;
     char* d_base = nullptr;
     CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_seeds), static_cast<size_t>(count) * 8, s));
     CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_base), static_cast<size_t>(count * n_units * unit_bytes), s));
     CUDA_TRY(cudaMemcpyAsync(d_seeds, seeds, static_cast<size_t>(count) * 8, cudaMemcpyHostToDevice, s));
     CUDA_TRY(vmt::launch_seed(variant, count, d_seeds, d_base, s));
+    vmt::JumpGrid gr{};
+    gr.count = count;
+    gr.lanes = lanes;
+    gr.base = d_base;
+    gr.unit_bytes = unit_bytes;
+    gr.states = static_cast<char*>(st->d_states);
+    gr.gen_bytes = vmt::state_bytes_per_gen(variant, lanes);
+    gr.row_deg = c.d_row_deg;
     if (any_jump) {
-        // base <- x^(d)(F) base, one base-256 digit per launch (jumps commute)
+        // base <- x^d(F) base, one base-256 digit per launch (jumps commute)
+        CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_jumps), static_cast<size_t>(count) * 8, s));
+        CUDA_TRY(cudaMemcpyAsync(d_jumps, jumps, static_cast<size_t>(count) * 8, cudaMemcpyHostToDevice, s));
+        gr.mode = vmt::JumpGrid::kDigit;
+        gr.jumps = d_jumps;
         for (int i = 0; i < 8; ++i) {
-            std::vector<vmt::JumpItem> items;
-            for (int64_t g = 0; g < count; ++g) {
-                const int dig = static_cast<int>((jumps[g] >> (8 * i)) & 255u);
-                if (!dig) continue;
-                vmt::JumpItem it{};
-                it.src = d_base + g * unit_bytes;
-                it.dst = d_base + g * unit_bytes;
-                it.src_stride = static_cast<int>(count);
-                it.dst_stride = static_cast<int>(count);
-                it.poly = 16 + 255 * i + dig - 1;
-                it.deg = c.row_deg[static_cast<size_t>(it.poly)];
-                items.push_back(it);
-            }
-            if ((rc = run_jump_items(variant, items, c.d_table, s))) return rc;
+            bool used = false;
+            for (int64_t g = 0; g < count && !used; ++g) used = ((jumps[g] >> (8 * i)) & 255u) != 0;
+            if (!used) continue;
+            gr.digit = i;
+            if ((rc = run_jump_grid(variant, gr, count, c.d_table, s))) return rc;
         }
     }
     // lane fan-out: lane t = x^(t J)(F) base, written into X-hat's column t
-    {
-        std::vector<vmt::JumpItem> items;
-        items.reserve(static_cast<size_t>(count * lanes));
-        const int64_t gen_bytes = vmt::state_bytes_per_gen(variant, lanes);
-        for (int64_t g = 0; g < count; ++g)
-            for (int t = 0; t < lanes; ++t) {
-                vmt::JumpItem it{};
-                it.src = d_base + g * unit_bytes;
-                it.src_stride = static_cast<int>(count);
-                it.dst = static_cast<char*>(st->d_states) + g * gen_bytes + t * unit_bytes;
-                it.dst_stride = lanes;
-                it.poly = t * 16 / lanes;
-                it.deg = c.row_deg[static_cast<size_t>(it.poly)];
-                items.push_back(it);
-            }
-        if ((rc = run_jump_items(variant, items, c.d_table, s))) return rc;
-    }
+    gr.mode = vmt::JumpGrid::kFanOut;
+    if ((rc = run_jump_grid(variant, gr, count * lanes, c.d_table, s))) return rc;
     CUDA_TRY(cudaFreeAsync(d_seeds, s));
     CUDA_TRY(cudaFreeAsync(d_base, s));
-    st->block_pos = vmt::block_words(variant, lanes);  // exhausted: the first output twists
+    if (d_jumps) CUDA_TRY(cudaFreeAsync(d_jumps, s));
     *out = st.release();
     return VMT_OK;
 }
@@ -667,18 +774,23 @@ int vmt_jump(vmt_state* st, const uint64_t* poly, int64_t nbits, void* cuda_stre
     if (!st || !poly) return fail(VMT_EINVAL, "null argument");
     if (nbits < 0 || nbits > 32 * vmt::kPolyWords - 64) return fail(VMT_EINVAL, "nbits out of range");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    std::vector<uint32_t> row(static_cast<size_t>(vmt::kPolyWords), 0);
+    // one device row holding the polynomial, followed by its degree
+    std::vector<uint32_t> row(static_cast<size_t>(vmt::kPolyWords) + 1, 0);
     const int64_t nw = (nbits + 63) / 64;
     Poly p(poly, poly + nw);
     if (nbits % 64 && nw) p[static_cast<size_t>(nw - 1)] &= (1ull << (nbits % 64)) - 1;
     to_rows(p, row.data());
     const int deg = vmt::gf2::degree(p);
+    std::memcpy(&row[static_cast<size_t>(vmt::kPolyWords)], &deg, sizeof(int));
     uint32_t* d_row = nullptr;
     CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_row), row.size() * 4, s));
     CUDA_TRY(cudaMemcpyAsync(d_row, row.data(), row.size() * 4, cudaMemcpyHostToDevice, s));
+    // every lane of every generator in place: the fan-out formula with the
+    // base being X-hat itself (unit stride = lanes) and row 0 for every lane
     std::vector<vmt::JumpItem> items;
-    const int64_t unit_bytes = static_cast<int64_t>(vmt::word_bytes(st->variant)) * vmt::words_per_unit(st->variant);
+    const int unit_bytes = vmt::word_bytes(st->variant) * vmt::words_per_unit(st->variant);
     const int64_t gen_bytes = vmt::state_bytes_per_gen(st->variant, st->lanes);
+    items.reserve(static_cast<size_t>(st->count * st->lanes));
     for (int64_t g = 0; g < st->count; ++g)
         for (int t = 0; t < st->lanes; ++t) {
             vmt::JumpItem it{};
@@ -690,9 +802,15 @@ int vmt_jump(vmt_state* st, const uint64_t* poly, int64_t nbits, void* cuda_stre
             it.deg = deg;
             items.push_back(it);
         }
-    int rc = run_jump_items(st->variant, items, d_row, s);
-    cudaFreeAsync(d_row, s);
-    return rc;
+    vmt::JumpItem* d_items = nullptr;
+    const size_t ib = items.size() * sizeof(vmt::JumpItem);
+    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_items), ib, s));
+    CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), ib, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(vmt::launch_jump(st->variant, d_items, static_cast<long long>(items.size()), d_row, s));
+    CUDA_TRY(cudaFreeAsync(d_items, s));
+    CUDA_TRY(cudaFreeAsync(d_row, s));
+    // the host vectors were staged by the copies above (pageable memory)
+    return VMT_OK;
 }
 
 int vmt_jump_poly(int variant, uint64_t d, int log2_extra, uint64_t* poly_out, int64_t cap_words)
@@ -791,20 +909,276 @@ int vmt_generate_host(vmt_state* st, int64_t n, int dtype, void* out_host, void*
     }
     CUDA_TRY(cudaStreamSynchronize(s));
     cudaStreamDestroy(cs);
-    if (rc == VMT_OK) st->block_pos = new_block_pos(vmt::block_words(st->variant, st->lanes), st->block_pos, n * words_per_output(st->variant, dtype));
+    if (rc == VMT_OK) advance_positions(st, 0, st->count, n * words_per_output(st->variant, dtype));
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// ragged and batched launches (one persistent launch over many generators of
+// different lengths; see include/vmt.h)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+// checks shared by the ragged and batched forms for generator g of st
+int check_unit(const vmt_state* st, int64_t g, int64_t n, int dtype, const void* out)
+{
+    if (dtype < VMT_U32 || dtype > VMT_F64) return fail(VMT_EINVAL, "bad dtype");
+    if (st->variant == VMT_MT19937_64 && dtype == VMT_U32)
+        return fail(VMT_EINVAL, "u32 output is not defined for MT19937-64");
+    if (n < 0) return fail(VMT_EINVAL, "negative count");
+    if (n > 0 && !out) return fail(VMT_EINVAL, "null output pointer");
+    const int wpo = words_per_output(st->variant, dtype);
+    if (n * wpo > kMaxUnitWords) return fail(VMT_EINVAL, "ragged/batched calls are limited to 2^30 words per generator");
+    if (wpo == 2 && n > 0 && ((st->h_pos[static_cast<size_t>(g)] & 1) != 0 || vector_width(st->variant, st->lanes) < 2))
+        return fail(VMT_EINVAL,
+                    "two-word outputs in ragged/batched calls need an even stream position and at least 2 lanes");
+    return VMT_OK;
+}
+
+}  // namespace
+
+struct vmt_batch {
+    struct Item {
+        vmt_state* st;
+        int64_t n;
+        int dtype;
+        char* out;
+    };
+    std::vector<Item> items;
+    // groups of units sharing (variant, lanes, dtype), contiguous in the unit array
+    struct Group {
+        int variant, lanes, dtype;
+        int64_t first, count;
+    };
+    std::vector<Group> groups;
+    vmt::UnitDesc* h_units = nullptr;
+    vmt::UnitDesc* d_units = nullptr;
+    int* d_counter = nullptr;
+    int64_t cap = 0;
+    cudaEvent_t free_ev = nullptr;
+    bool built = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t capture_stream = nullptr;
+};
+
+namespace {
+
+int batch_build(vmt_batch* b)
+{
+    // units grouped by kernel, longest first inside a group
+    std::vector<std::pair<std::tuple<int, int, int>, vmt::UnitDesc>> all;
+    for (const auto& it : b->items) {
+        vmt_state* st = it.st;
+        const int64_t gen_bytes = vmt::state_bytes_per_gen(st->variant, st->lanes);
+        const int64_t words = it.n * words_per_output(st->variant, it.dtype);
+        const int eb = elem_bytes(it.dtype);
+        if (words == 0) continue;
+        for (int64_t g = 0; g < st->count; ++g) {
+            vmt::UnitDesc u{};
+            u.state = static_cast<char*>(st->d_states) + g * gen_bytes;
+            u.pos = st->d_pos + g;
+            u.total = words;
+            u.out = it.out + g * it.n * eb;
+            all.push_back({std::make_tuple(st->variant, st->lanes, it.dtype), u});
+        }
+    }
+    std::stable_sort(all.begin(), all.end(), [](const auto& x, const auto& y) {
+        if (x.first != y.first) return x.first < y.first;
+        return x.second.total > y.second.total;
+    });
+    int rc = reserve_units(&b->h_units, &b->d_units, &b->d_counter, &b->cap, &b->free_ev,
+                           static_cast<int64_t>(all.size()));
+    if (rc) return rc;
+    b->groups.clear();
+    for (size_t i = 0; i < all.size(); ++i) {
+        b->h_units[i] = all[i].second;
+        if (b->groups.empty() || std::make_tuple(b->groups.back().variant, b->groups.back().lanes,
+                                                 b->groups.back().dtype) != all[i].first) {
+            if (b->groups.size() == 16) return fail(VMT_EINVAL, "a batch may mix at most 16 kernel groups");
+            b->groups.push_back({std::get<0>(all[i].first), std::get<1>(all[i].first), std::get<2>(all[i].first),
+                                 static_cast<int64_t>(i), 0});
+        }
+        b->groups.back().count++;
+    }
+    b->built = true;
+    return VMT_OK;
+}
+
+int batch_enqueue(vmt_batch* b, cudaStream_t s)
+{
+    const int64_t n = b->groups.empty() ? 0 : b->groups.back().first + b->groups.back().count;
+    if (n == 0) return VMT_OK;
+    CUDA_TRY(cudaMemcpyAsync(b->d_units, b->h_units, static_cast<size_t>(n) * sizeof(vmt::UnitDesc),
+                             cudaMemcpyHostToDevice, s));
+    for (size_t k = 0; k < b->groups.size(); ++k) {
+        const auto& gr = b->groups[k];
+        const int rc = launch_units(gr.variant, gr.lanes, gr.dtype, b->d_units + gr.first, gr.count,
+                                    b->d_counter + k, s);
+        if (rc) return rc;
+    }
+    return VMT_OK;
+}
+
+void batch_advance(vmt_batch* b)
+{
+    for (const auto& it : b->items) {
+        advance_positions(it.st, 0, it.st->count, it.n * words_per_output(it.st->variant, it.dtype));
+        refresh_uniform(it.st);
+    }
+}
+
+int batch_check(vmt_batch* b)
+{
+    for (const auto& it : b->items)
+        for (int64_t g = 0; g < it.st->count; ++g) {
+            const int rc = check_unit(it.st, g, it.n, it.dtype, it.out);
+            if (rc) return rc;
+        }
+    return VMT_OK;
+}
+
+void batch_drop_graph(vmt_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vmt_generate_ragged(vmt_state* st, const int64_t* n, int dtype, void* const* outs, void* cuda_stream)
+{
+    if (!st || !n || !outs) return fail(VMT_EINVAL, "null argument");
+    for (int64_t g = 0; g < st->count; ++g) {
+        const int rc = check_unit(st, g, n[g], dtype, outs[g]);
+        if (rc) return rc;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int rc = reserve_units(&st->h_units, &st->d_units, &st->d_counter, &st->units_cap, &st->units_free, st->count);
+    if (rc) return rc;
+    const int wpo = words_per_output(st->variant, dtype);
+    const int64_t gen_bytes = vmt::state_bytes_per_gen(st->variant, st->lanes);
+    int64_t k = 0;
+    for (int64_t g = 0; g < st->count; ++g) {
+        if (n[g] == 0) continue;
+        vmt::UnitDesc& u = st->h_units[k++];
+        u.state = static_cast<char*>(st->d_states) + g * gen_bytes;
+        u.pos = st->d_pos + g;
+        u.total = n[g] * wpo;
+        u.out = static_cast<char*>(outs[g]);
+    }
+    std::stable_sort(st->h_units, st->h_units + k,
+                     [](const vmt::UnitDesc& x, const vmt::UnitDesc& y) { return x.total > y.total; });
+    CUDA_TRY(cudaMemcpyAsync(st->d_units, st->h_units, static_cast<size_t>(k) * sizeof(vmt::UnitDesc),
+                             cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaEventRecord(st->units_free, s));
+    rc = launch_units(st->variant, st->lanes, dtype, st->d_units, k, st->d_counter, s);
+    if (rc) return rc;
+    for (int64_t g = 0; g < st->count; ++g) advance_positions(st, g, 1, n[g] * wpo);
+    refresh_uniform(st);
+    return VMT_OK;
+}
+
+int vmt_batch_create(vmt_batch** b)
+{
+    if (!b) return fail(VMT_EINVAL, "null handle");
+    *b = new vmt_batch();
+    return VMT_OK;
+}
+
+int vmt_batch_add(vmt_batch* b, vmt_state* st, int64_t n, int dtype, void* out_dev)
+{
+    if (!b || !st) return fail(VMT_EINVAL, "null argument");
+    for (const auto& it : b->items)
+        if (it.st == st) return fail(VMT_EINVAL, "a state may appear once per batch");
+    for (int64_t g = 0; g < st->count; ++g) {
+        const int rc = check_unit(st, g, n, dtype, out_dev);
+        if (rc) return rc;
+    }
+    b->items.push_back({st, n, dtype, static_cast<char*>(out_dev)});
+    b->built = false;
+    batch_drop_graph(b);
+    return VMT_OK;
+}
+
+int vmt_batch_run(vmt_batch* b, void* cuda_stream)
+{
+    if (!b) return fail(VMT_EINVAL, "null batch");
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (!b->built && (rc = batch_build(b))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if ((rc = batch_enqueue(b, s))) return rc;
+    CUDA_TRY(cudaEventRecord(b->free_ev, s));
+    batch_advance(b);
+    return VMT_OK;
+}
+
+int vmt_batch_run_graph(vmt_batch* b, void* cuda_stream)
+{
+    if (!b) return fail(VMT_EINVAL, "null batch");
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (!b->built && (rc = batch_build(b))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (!b->exec) {
+        if (!b->capture_stream) CUDA_TRY(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
+        CUDA_TRY(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
+        rc = batch_enqueue(b, b->capture_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->capture_stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(VMT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        b->graph = g;
+        CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    }
+    CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    CUDA_TRY(cudaEventRecord(b->free_ev, s));
+    batch_advance(b);
+    return VMT_OK;
+}
+
+int vmt_batch_clear(vmt_batch* b)
+{
+    if (!b) return fail(VMT_EINVAL, "null batch");
+    b->items.clear();
+    b->groups.clear();
+    b->built = false;
+    batch_drop_graph(b);
+    return VMT_OK;
+}
+
+void vmt_batch_destroy(vmt_batch* b)
+{
+    if (!b) return;
+    if (b->free_ev) cudaEventSynchronize(b->free_ev), cudaEventDestroy(b->free_ev);
+    batch_drop_graph(b);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->h_units) cudaFreeHost(b->h_units);
+    if (b->d_units) cudaFree(b->d_units);
+    if (b->d_counter) cudaFree(b->d_counter);
+    delete b;
 }
 
 struct ExportHeader {
     char magic[8];
     int32_t version, variant, lanes, pad;
-    int64_t count, block_pos, state_bytes;
+    int64_t count, reserved, state_bytes;
 };
 
 int64_t vmt_state_bytes(const vmt_state* st)
 {
     if (!st) return fail(VMT_EINVAL, "null state");
-    return static_cast<int64_t>(sizeof(ExportHeader)) + state_total_bytes(st);
+    return static_cast<int64_t>(sizeof(ExportHeader)) + state_total_bytes(st) + st->count * 8;
 }
 
 int vmt_state_export(const vmt_state* st, void* host_buf, size_t cap, void* cuda_stream)
@@ -813,18 +1187,20 @@ int vmt_state_export(const vmt_state* st, void* host_buf, size_t cap, void* cuda
     const int64_t need = vmt_state_bytes(st);
     if (static_cast<int64_t>(cap) < need) return fail(VMT_EINVAL, "buffer too small");
     ExportHeader h{};
-    std::memcpy(h.magic, "VMTSTAT1", 8);
-    h.version = 1;
+    std::memcpy(h.magic, "VMTSTAT2", 8);
+    h.version = 2;
     h.variant = st->variant;
     h.lanes = st->lanes;
     h.count = st->count;
-    h.block_pos = st->block_pos;
     h.state_bytes = state_total_bytes(st);
     std::memcpy(host_buf, &h, sizeof(h));
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(host_buf) + sizeof(h), st->d_states, static_cast<size_t>(h.state_bytes),
                              cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    // per-generator stream positions follow the states
+    std::memcpy(static_cast<char*>(host_buf) + sizeof(h) + h.state_bytes, st->h_pos.data(),
+                static_cast<size_t>(st->count) * 8);
     return VMT_OK;
 }
 
@@ -834,19 +1210,27 @@ int vmt_state_import(vmt_state* st, const void* host_buf, size_t len, void* cuda
     if (len < sizeof(ExportHeader)) return fail(VMT_ESTATE, "buffer shorter than the header");
     ExportHeader h{};
     std::memcpy(&h, host_buf, sizeof(h));
-    if (std::memcmp(h.magic, "VMTSTAT1", 8) != 0 || h.version != 1) return fail(VMT_ESTATE, "not a vmt state export");
+    if (std::memcmp(h.magic, "VMTSTAT2", 8) != 0 || h.version != 2) return fail(VMT_ESTATE, "not a vmt state export");
     if (h.variant != st->variant || h.lanes != st->lanes || h.count != st->count ||
         h.state_bytes != state_total_bytes(st))
         return fail(VMT_ESTATE, "export does not match this state object");
-    if (static_cast<int64_t>(len) < static_cast<int64_t>(sizeof(h)) + h.state_bytes)
+    if (static_cast<int64_t>(len) < static_cast<int64_t>(sizeof(h)) + h.state_bytes + h.count * 8)
         return fail(VMT_ESTATE, "truncated export");
     const int64_t B = vmt::block_words(st->variant, st->lanes);
-    if (h.block_pos < 0 || h.block_pos > B) return fail(VMT_ESTATE, "block position out of range");
+    std::vector<int64_t> pos(static_cast<size_t>(h.count));
+    std::memcpy(pos.data(), static_cast<const char*>(host_buf) + sizeof(h) + h.state_bytes, pos.size() * 8);
+    std::vector<int> pos32(pos.size());
+    for (size_t g = 0; g < pos.size(); ++g) {
+        if (pos[g] < 0 || pos[g] > B) return fail(VMT_ESTATE, "block position out of range");
+        pos32[g] = static_cast<int>(pos[g]);
+    }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     CUDA_TRY(cudaMemcpyAsync(st->d_states, static_cast<const char*>(host_buf) + sizeof(h),
                              static_cast<size_t>(h.state_bytes), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(st->d_pos, pos32.data(), pos32.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    st->block_pos = h.block_pos;
+    st->h_pos = pos;
+    refresh_uniform(st);
     return VMT_OK;
 }
 
@@ -856,7 +1240,7 @@ int vmt_state_info(const vmt_state* st, int* variant, int* lanes, int64_t* count
     if (variant) *variant = st->variant;
     if (lanes) *lanes = st->lanes;
     if (count) *count = st->count;
-    if (block_pos) *block_pos = st->block_pos;
+    if (block_pos) *block_pos = st->h_pos.empty() ? 0 : st->h_pos[0];
     return VMT_OK;
 }
 
@@ -874,6 +1258,11 @@ void vmt_free(vmt_state* st)
 {
     if (!st) return;
     if (st->d_states) cudaFree(st->d_states);
+    if (st->d_pos) cudaFree(st->d_pos);
+    if (st->units_free) cudaEventSynchronize(st->units_free), cudaEventDestroy(st->units_free);
+    if (st->h_units) cudaFreeHost(st->h_units);
+    if (st->d_units) cudaFree(st->d_units);
+    if (st->d_counter) cudaFree(st->d_counter);
     delete st;
 }
 

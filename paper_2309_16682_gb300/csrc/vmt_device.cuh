@@ -108,12 +108,25 @@ __device__ __forceinline__ double f64_of_pair(uint32_t a, uint32_t b)
 __device__ __forceinline__ float f32_of_u64(unsigned long long z) { return f32_of_u32(static_cast<uint32_t>(z >> 32)); }
 
 // ----------------------------------------------------------------------------
-// Emitter: routes word e (call-relative index in the V-stream) of generator g
-// to its segment, converts it and stores it.
+// Emitter: routes word e (call-relative index in the V-stream) of one
+// generator to its segment, converts it and stores it.  In lock-step launches
+// generator g's outputs of segment s start at seg[s].out + g*seg[s].count
+// elements; in unit launches the unit's single segment starts at unit_out.
 // ----------------------------------------------------------------------------
+__device__ __forceinline__ int elem_size(int dt) { return (dt == VMT_U32 || dt == VMT_F32) ? 4 : 8; }
+
 struct Emitter {
     const GenArgs& a;
-    long long g;  // generator index within the output arrays
+    long long g;      // generator index within the output arrays (lock-step)
+    char* unit_out;   // unit mode: first output element of the unit, else nullptr
+
+    // address of this generator's first output element of segment s
+    __device__ __forceinline__ char* elem0(int s) const
+    {
+        if (unit_out) return unit_out;
+        const SegArg& sg = a.seg[s];
+        return sg.out + g * sg.count * elem_size(sg.dtype);
+    }
 
     __device__ __forceinline__ int seg_of(long long e) const
     {
@@ -131,93 +144,26 @@ struct Emitter {
                                            long long ebase) const
     {
         const long long e0 = ebase + f0 - lo;
-        if (f0 >= lo && f0 + VW <= hi) {
-            const int s = seg_of(e0);
-            const SegArg& sg = a.seg[s];
-            const long long rel = e0 - sg.wbeg;
-            if (sg.fast && e0 + VW <= sg.wend && (rel % VW) == 0) {
-                store_vec32<VW>(sg, rel, z);
-                return;
-            }
-        }
 #pragma unroll
         for (int u = 0; u < VW; ++u) {
             const long long f = f0 + u;
             if (f < lo || f >= hi) continue;
             const long long e = e0 + u;
-            const SegArg& sg = a.seg[seg_of(e)];
+            const int s = seg_of(e);
+            const SegArg& sg = a.seg[s];
             const long long rel = e - sg.wbeg;
-            char* base = sg.out;
-            const long long idx = g * sg.count;
+            char* base = elem0(s);
             switch (sg.dtype) {
-            case VMT_U32: reinterpret_cast<uint32_t*>(base)[idx + rel] = z[u]; break;
-            case VMT_F32: reinterpret_cast<float*>(base)[idx + rel] = f32_of_u32(z[u]); break;
+            case VMT_U32: reinterpret_cast<uint32_t*>(base)[rel] = z[u]; break;
+            case VMT_F32: reinterpret_cast<float*>(base)[rel] = f32_of_u32(z[u]); break;
             case VMT_U64:
                 if ((rel & 1) == 0 && u + 1 < VW)
-                    reinterpret_cast<unsigned long long*>(base)[idx + rel / 2] =
+                    reinterpret_cast<unsigned long long*>(base)[rel / 2] =
                         static_cast<unsigned long long>(z[u]) | (static_cast<unsigned long long>(z[u + 1]) << 32);
                 break;
             case VMT_F64:
-                if ((rel & 1) == 0 && u + 1 < VW)
-                    reinterpret_cast<double*>(base)[idx + rel / 2] = f64_of_pair(z[u], z[u + 1]);
+                if ((rel & 1) == 0 && u + 1 < VW) reinterpret_cast<double*>(base)[rel / 2] = f64_of_pair(z[u], z[u + 1]);
                 break;
-            }
-        }
-    }
-
-    template <int VW>
-    __device__ __forceinline__ void store_vec32(const SegArg& sg, long long rel, const uint32_t (&z)[VW]) const
-    {
-        char* base = sg.out;
-        const long long idx = g * sg.count;
-        if (VW == 4) {
-            switch (sg.dtype) {
-            case VMT_U32:
-                __stcs(reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(base) + idx + rel),
-                       make_uint4(z[0], z[1 % VW], z[2 % VW], z[3 % VW]));
-                break;
-            case VMT_F32:
-                __stcs(reinterpret_cast<float4*>(reinterpret_cast<float*>(base) + idx + rel),
-                       make_float4(f32_of_u32(z[0]), f32_of_u32(z[1 % VW]), f32_of_u32(z[2 % VW]),
-                                   f32_of_u32(z[3 % VW])));
-                break;
-            case VMT_U64: {
-                ulonglong2 v;
-                v.x = static_cast<unsigned long long>(z[0]) | (static_cast<unsigned long long>(z[1 % VW]) << 32);
-                v.y = static_cast<unsigned long long>(z[2 % VW]) | (static_cast<unsigned long long>(z[3 % VW]) << 32);
-                __stcs(reinterpret_cast<ulonglong2*>(reinterpret_cast<unsigned long long*>(base) + idx + rel / 2), v);
-                break;
-            }
-            case VMT_F64: {
-                double2 v;
-                v.x = f64_of_pair(z[0], z[1 % VW]);
-                v.y = f64_of_pair(z[2 % VW], z[3 % VW]);
-                __stcs(reinterpret_cast<double2*>(reinterpret_cast<double*>(base) + idx + rel / 2), v);
-                break;
-            }
-            }
-        } else if (VW == 2) {
-            switch (sg.dtype) {
-            case VMT_U32:
-                __stcs(reinterpret_cast<uint2*>(reinterpret_cast<uint32_t*>(base) + idx + rel), make_uint2(z[0], z[1 % VW]));
-                break;
-            case VMT_F32:
-                __stcs(reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + idx + rel),
-                       make_float2(f32_of_u32(z[0]), f32_of_u32(z[1 % VW])));
-                break;
-            case VMT_U64:
-                __stcs(reinterpret_cast<unsigned long long*>(base) + idx + rel / 2,
-                       static_cast<unsigned long long>(z[0]) | (static_cast<unsigned long long>(z[1 % VW]) << 32));
-                break;
-            case VMT_F64:
-                __stcs(reinterpret_cast<double*>(base) + idx + rel / 2, f64_of_pair(z[0], z[1 % VW]));
-                break;
-            }
-        } else {
-            switch (sg.dtype) {
-            case VMT_U32: __stcs(reinterpret_cast<uint32_t*>(base) + idx + rel, z[0]); break;
-            case VMT_F32: __stcs(reinterpret_cast<float*>(base) + idx + rel, f32_of_u32(z[0])); break;
-            default: break;  // pairs never take the one-word vector path
             }
         }
     }
@@ -228,49 +174,19 @@ struct Emitter {
                                            long long hi, long long ebase) const
     {
         const long long e0 = ebase + f0 - lo;
-        if (f0 >= lo && f0 + VW <= hi) {
-            const int s = seg_of(e0);
-            const SegArg& sg = a.seg[s];
-            const long long rel = e0 - sg.wbeg;
-            if (sg.fast && e0 + VW <= sg.wend && (rel % VW) == 0) {
-                char* base = sg.out;
-                const long long idx = g * sg.count + rel;
-                if (VW == 2) {
-                    switch (sg.dtype) {
-                    case VMT_U64: {
-                        ulonglong2 v;
-                        v.x = z[0];
-                        v.y = z[1 % VW];
-                        __stcs(reinterpret_cast<ulonglong2*>(reinterpret_cast<unsigned long long*>(base) + idx), v);
-                        return;
-                    }
-                    case VMT_F64: {
-                        double2 v;
-                        v.x = f64_of_u64(z[0]);
-                        v.y = f64_of_u64(z[1 % VW]);
-                        __stcs(reinterpret_cast<double2*>(reinterpret_cast<double*>(base) + idx), v);
-                        return;
-                    }
-                    case VMT_F32:
-                        __stcs(reinterpret_cast<float2*>(reinterpret_cast<float*>(base) + idx),
-                               make_float2(f32_of_u64(z[0]), f32_of_u64(z[1 % VW])));
-                        return;
-                    }
-                }
-            }
-        }
 #pragma unroll
         for (int u = 0; u < VW; ++u) {
             const long long f = f0 + u;
             if (f < lo || f >= hi) continue;
             const long long e = e0 + u;
-            const SegArg& sg = a.seg[seg_of(e)];
-            const long long idx = g * sg.count + (e - sg.wbeg);
-            char* base = sg.out;
+            const int s = seg_of(e);
+            const SegArg& sg = a.seg[s];
+            const long long rel = e - sg.wbeg;
+            char* base = elem0(s);
             switch (sg.dtype) {
-            case VMT_U64: reinterpret_cast<unsigned long long*>(base)[idx] = z[u]; break;
-            case VMT_F64: reinterpret_cast<double*>(base)[idx] = f64_of_u64(z[u]); break;
-            case VMT_F32: reinterpret_cast<float*>(base)[idx] = f32_of_u64(z[u]); break;
+            case VMT_U64: reinterpret_cast<unsigned long long*>(base)[rel] = z[u]; break;
+            case VMT_F64: reinterpret_cast<double*>(base)[rel] = f64_of_u64(z[u]); break;
+            case VMT_F32: reinterpret_cast<float*>(base)[rel] = f32_of_u64(z[u]); break;
             default: break;
             }
         }

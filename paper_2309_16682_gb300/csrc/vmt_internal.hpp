@@ -30,15 +30,27 @@ struct SegArg {
     int fast;  // out and count*elem_size are multiples of 16 bytes
 };
 
+// One unit of a ragged or batched launch: one generator with its own state,
+// stream position, length and output (a single segment of type seg[0].dtype).
+struct UnitDesc {
+    char* state;         // X-hat of the generator
+    int* pos;            // its block position (read at start, written at end)
+    long long total;     // native words to produce
+    char* out;           // first output element
+};
+
 struct GenArgs {
-    void* states;      // [gens][block words]
-    long long gens;    // generators in the launch
-    long long gen0;    // first generator's index in the output arrays
-    int pos;           // block position (native words) at call start, same for all
-    long long total;   // native words per generator in this call
+    void* states;      // [gens][block words] (lock-step mode)
+    long long gens;    // generators (lock-step) or units (unit mode) in the launch
+    long long gen0;    // first generator's index in the output arrays (lock-step mode)
+    int pos;           // lock-step mode: the block position shared by all generators
+    int* pos_dev;      // lock-step mode: per-generator block positions, written at end
+    long long total;   // native words per generator in this call (lock-step mode)
     int nseg;
     SegArg seg[VMT_MAXSEG];
     int threads;       // CTA size among the compiled ones (0: default), set by the tuning table
+    const UnitDesc* units;   // unit mode when non-null: one entry per unit, longest first
+    int* work_counter;       // unit mode: next unit = atomicAdd(work_counter, 1) (zeroed before launch)
 };
 
 // Jump work item: dst = c(F) src for one lane-state.  Unit u of the source
@@ -55,9 +67,32 @@ struct JumpItem {
 
 constexpr int kPolyWords = 640;  // u32 words per polynomial row (20480 bits)
 
-cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, cudaStream_t s);
+// Jump work items described by a formula instead of a list (so that
+// initialisation needs no host-built arrays):
+//   kFanOut: item g*lanes + t writes lane t of generator g's X-hat as
+//            row t*16/lanes applied to g's base state (unit-major base);
+//   kDigit:  item g applies row 16 + 255*digit + d - 1 in place to g's base
+//            state, d = byte `digit` of jumps[g] (nothing when d = 0).
+struct JumpGrid {
+    enum { kFanOut = 1, kDigit = 2 };
+    int mode;
+    long long count;
+    int lanes;
+    char* base;
+    int unit_bytes;
+    char* states;
+    long long gen_bytes;
+    const unsigned long long* jumps;
+    int digit;
+    const int* row_deg;
+};
+
+// ragged: generators of one launch may differ in position or length
+cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, bool ragged, cudaStream_t s);
 cudaError_t launch_seed(int variant, long long count, const unsigned long long* seeds, void* base, cudaStream_t s);
 cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s);
+cudaError_t launch_jump_grid(int variant, const JumpGrid& gr, long long nitems, const uint32_t* polys, cudaStream_t s);
+cudaError_t launch_fill_int(int* p, long long n, int value, cudaStream_t s);
 
 // tuned CTA size for a (variant, lanes) pair (0: the kernel's default)
 int tuned_threads(int variant, int lanes);

@@ -240,3 +240,42 @@ def test_every_cta_size_gives_the_same_stream(vmt, variant, M, threads):
     for k in range(len(segs)):
         assert np.array_equal(got[k], ref[k])
     assert vmt.device_status() == 0
+
+
+@pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])
+def test_ragged_then_lockstep(vmt, oracle_polys, variant):
+    """Per-generator lengths in one persistent launch, then a lock-step call
+    continues every generator from its own position."""
+    M = 4
+    seeds = I.splitmix64(300 + variant, 5)
+    native = "u64" if variant == O.MT64 else "u32"
+    g = vmt.VGenerator(VNAME[variant], M, seeds)
+    n1 = [0, 2, 1000, 7778, 20000]
+    r = [_np(t) for t in g.generate_ragged(n1, native)]
+    n2 = 3002
+    tail = _np(g.generate(n2, native))
+    for gi, s in enumerate(seeds):
+        ref = _expected(variant, M, int(s), [(n1[gi] + n2, native)])[0]
+        _assert_same(r[gi], ref[:n1[gi]], f"ragged gen {gi}")
+        _assert_same(tail[gi], ref[n1[gi]:], f"lock-step after ragged gen {gi}")
+
+
+def test_batch_and_graph_match_plain_calls(vmt):
+    """A batch over three state objects (three kernels), run plainly and
+    through a replayed CUDA graph, equals the same calls made one by one."""
+    spec = [("mt32", 16, I.splitmix64(1, 2), 5000, "u32"), ("mt64", 8, I.splitmix64(2, 3), 3000, "f64"),
+            ("sfmt", 4, I.splitmix64(3, 2), 7004, "u32")]
+    gens = [vmt.VGenerator(v, m, s) for v, m, s, _, _ in spec]
+    twins = [vmt.VGenerator(v, m, s) for v, m, s, _, _ in spec]
+    outs = [torch.empty((len(s), n), dtype=vmt._torch_dtype(dt), device="cuda") for _, _, s, n, dt in spec]
+    b = vmt.Batch()
+    for gen, out, (_, _, _, n, dt) in zip(gens, outs, spec):
+        b.add(gen, n, dt, out)
+    for rnd in range(4):
+        b.run(graph=rnd >= 2)
+        got = [_np(o) for o in outs]
+        for k, (twin, (_, _, _, n, dt)) in enumerate(zip(twins, spec)):
+            ref = _np(twin.generate(n, dt))
+            assert np.array_equal(got[k], ref), (rnd, k)
+    b.close()
+    assert vmt.device_status() == 0
