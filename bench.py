@@ -221,6 +221,87 @@ def run_reference(args, world, rank):
 
 
 # ---------------------------------------------------------------------------
+# served mix: Poisson arrivals, the continuous-batching server against the
+# plain form (each request initialised and generated on its own, in arrival
+# order, one after another)
+# ---------------------------------------------------------------------------
+NAMES = {0: "mt32", 1: "mt64", 2: "sfmt"}
+
+
+def _pct(x, q):
+    return float(np.percentile(np.asarray(x), q)) if len(x) else None
+
+
+def run_served(vmt, requests: int, rate: float, plain_requests: int):
+    import torch
+    tr = I.request_trace(requests, rate_per_s=rate)
+    native = {0: "u32", 1: "u64", 2: "u32"}
+    reqs = [(NAMES[int(tr["variant"][i])], int(tr["lanes"][i]), native[int(tr["variant"][i])],
+             int(tr["seed"][i]), int(tr["jump"][i]), int(tr["n"][i]), float(tr["arrival_s"][i]))
+            for i in range(requests)]
+    esize = {"u32": 4, "u64": 8}
+    srv = vmt.Server(state_budget=16 << 30, output_budget=96 << 30, max_batch=4096)
+    # warm-up: polynomial tables of every variant and digit tables
+    for v in ("mt32", "mt64", "sfmt"):
+        rid = srv.submit(v, 4, native[{"mt32": 0, "mt64": 1, "sfmt": 2}[v]], 1, 12345, 1000)
+        srv.wait(rid)
+        srv.release(rid)
+    torch.cuda.synchronize()
+    import threading as th
+    ids = [None] * requests
+    lat = [0.0] * requests
+    done_at = [0.0] * requests
+
+    def releaser():
+        for i in range(requests):
+            while ids[i] is None:
+                time.sleep(20e-6)
+            srv.wait(ids[i])
+            done_at[i] = time.perf_counter()
+            lat[i] = srv.poll(ids[i])[3]
+            srv.release(ids[i])
+
+    rt = th.Thread(target=releaser)
+    rt.start()
+    t0 = time.perf_counter()
+    for i, (v, m, dt, seed, jump, n, arr) in enumerate(reqs):
+        while time.perf_counter() - t0 < arr:
+            pass
+        ids[i] = srv.submit(v, m, dt, seed, jump, n)
+    rt.join()
+    t_end = max(done_at)
+    stats = srv.stats()
+    srv.close()
+    total_bytes = sum(n * esize[dt] for (_, _, dt, _, _, n, _) in reqs)
+    batched = {"p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99),
+               "throughput_GBps": total_bytes / (t_end - t0) / 1e9, "batches": stats["batches"],
+               "peak_output_bytes": stats["peak_output_bytes"], "wall_s": t_end - t0}
+    # plain form on the first plain_requests requests of the same trace
+    pr = reqs[:plain_requests]
+    plat = []
+    pbytes = 0
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    for (v, m, dt, seed, jump, n, arr) in pr:
+        while time.perf_counter() - t0 < arr:
+            pass
+        g = vmt.VGenerator(v, m, [seed], [jump])
+        out = g.generate(n, dt)
+        stream.synchronize()
+        plat.append(time.perf_counter() - t0 - arr)
+        pbytes += n * esize[dt]
+        g.close()
+        del out
+    p_wall = time.perf_counter() - t0
+    plain = {"p50_ms": 1e3 * _pct(plat, 50), "p99_ms": 1e3 * _pct(plat, 99), "throughput_GBps": pbytes / p_wall / 1e9,
+             "requests": len(pr), "wall_s": p_wall}
+    return {"requests": requests, "arrival_rate_per_s": rate, "lanes": "4/8/16", "length_words": "log-uniform 1e3..1e8",
+            "batched": batched, "plain": plain,
+            "note": "latency = submit (at the trace's arrival time) to completion; plain = one request at a time, "
+                    "vmt_init + vmt_generate + synchronise, on a prefix of the same trace"}
+
+
+# ---------------------------------------------------------------------------
 # GB300 arm
 # ---------------------------------------------------------------------------
 def run_gb300(args, world, rank, local):
@@ -300,6 +381,10 @@ def run_gb300(args, world, rank, local):
                "d2h_bytes_per_step": out_bytes, "steps": e2e_steps}
         del hosts
 
+    served = None
+    if not args.no_serve:
+        served = run_served(vmt, args.serve_requests, 2.0e4, args.plain_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle as O
@@ -338,6 +423,7 @@ def run_gb300(args, world, rank, local):
                      "note": "seed + jump-ahead de-phasing before the timed region (first call also loads or "
                              "computes the jump polynomials)"},
             "clocks": clocks,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
 
@@ -351,6 +437,9 @@ def main():
     ap.add_argument("--workload", default="vmt32_m16_g65536", choices=sorted(I.WORKLOADS))
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--tune", action="store_true", help="run the autotuner before timing")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-mix measurement")
+    ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--plain-requests", type=int, default=1000)
     ap.add_argument("--generators", type=int, default=0,
                     help="smaller generator count (profiling cases); default: the workload's")
     ap.add_argument("--no-e2e", action="store_true")

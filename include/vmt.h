@@ -155,6 +155,59 @@ int vmt_batch_clear(vmt_batch* b);
 void vmt_batch_destroy(vmt_batch* b);
 
 /*
+ * Serving (the paper has no counterpart; it serves the paper's generators to
+ * many independent clients).  A request asks for n outputs of type dtype from
+ * one fresh V-generator (variant, lanes, seed, jump as in vmt_init).  Requests
+ * are admitted FIFO while two budgets hold: generator states of batches in
+ * flight (state_budget_bytes) and outputs not yet released
+ * (output_budget_bytes).  A worker thread launches admitted requests as soon
+ * as they arrive, at most max_batch (1..4096) per batch: batched seeding and
+ * jump-ahead on one stream, a persistent ragged generation (longest first) on
+ * another, so a new batch's initialisation overlaps the previous batch's
+ * generation.
+ *   vmt_server_submit   never blocks; *id names the request
+ *   vmt_server_poll     status VMT_SERVER_QUEUED / RUNNING / DONE or a negative
+ *                       VMT_E* code (that request failed; the server goes on);
+ *                       when DONE, *out_dev is the device buffer (n elements)
+ *                       and *latency_s the time from submit to completion
+ *   vmt_server_wait     blocks until the request is done or failed, or returns
+ *                       VMT_ETIMEOUT after timeout_ms
+ *   vmt_server_release  frees the output (after the client's own work on it
+ *                       has finished) and returns its bytes to the budget
+ * Limits: n * words-per-output <= 2^30; u64/f64 from 32-bit generators need
+ * lanes >= 2.  A request larger than a budget fails with VMT_ENOMEM.
+ */
+#define VMT_SERVER_QUEUED 0
+#define VMT_SERVER_RUNNING 1
+#define VMT_SERVER_DONE 2
+
+typedef struct vmt_server vmt_server;
+typedef struct {
+    int64_t state_budget_bytes;
+    int64_t output_budget_bytes;
+    int max_batch;
+} vmt_server_config;
+typedef struct {
+    int variant, lanes, dtype;
+    uint64_t seed, jump;
+    int64_t n;
+} vmt_request;
+typedef struct {
+    int64_t queued, in_flight_batches, batches, completed, failed, bytes_out;
+    int64_t state_bytes_in_use, output_bytes_in_use, peak_state_bytes, peak_output_bytes;
+} vmt_server_counters;
+
+int vmt_server_create(vmt_server** s, const vmt_server_config* cfg);
+int vmt_server_submit(vmt_server* s, const vmt_request* r, uint64_t* id);
+int vmt_server_poll(vmt_server* s, uint64_t id, int* status, void** out_dev, int64_t* bytes, double* latency_s);
+int vmt_server_wait(vmt_server* s, uint64_t id, int timeout_ms);
+int vmt_server_release(vmt_server* s, uint64_t id);
+/* copy a finished request's output into host memory (cap bytes; synchronous) */
+int vmt_server_copy(vmt_server* s, uint64_t id, void* host_buf, int64_t cap);
+int vmt_server_stats(vmt_server* s, vmt_server_counters* stats);
+void vmt_server_destroy(vmt_server* s);
+
+/*
  * vmt_generate_host -- as vmt_generate but into host memory (pinned or
  * pageable): the words are generated into a device staging buffer in chunks
  * and copied to out_host, generation of one chunk overlapping the copy of the

@@ -76,6 +76,14 @@ def lib() -> ctypes.CDLL:
             "vmt_batch_run_graph": (I, [P, P]),
             "vmt_batch_clear": (I, [P]),
             "vmt_batch_destroy": (None, [P]),
+            "vmt_server_create": (I, [PP, P]),
+            "vmt_server_submit": (I, [P, P, P]),
+            "vmt_server_poll": (I, [P, U64, P, P, P, P]),
+            "vmt_server_wait": (I, [P, U64, I]),
+            "vmt_server_release": (I, [P, U64]),
+            "vmt_server_copy": (I, [P, U64, P, I64]),
+            "vmt_server_stats": (I, [P, P]),
+            "vmt_server_destroy": (None, [P]),
             "vmt_tune_set": (I, [I, I, I]),
             "vmt_tune_get": (I, [I, I]),
             "vmt_autotune": (I, [I, I, I64, I64, I, I, P, P, P]),
@@ -238,6 +246,78 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             lib().vmt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+SERVER_QUEUED, SERVER_RUNNING, SERVER_DONE = 0, 1, 2
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("state_budget_bytes", ctypes.c_int64), ("output_budget_bytes", ctypes.c_int64),
+                ("max_batch", ctypes.c_int)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("lanes", ctypes.c_int), ("dtype", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("jump", ctypes.c_uint64), ("n", ctypes.c_int64)]
+
+
+class _Counters(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("queued", "in_flight_batches", "batches", "completed", "failed",
+                                             "bytes_out", "state_bytes_in_use", "output_bytes_in_use",
+                                             "peak_state_bytes", "peak_output_bytes")]
+
+
+class Server:
+    """Continuous-batching request server (vmt_server_*)."""
+
+    def __init__(self, state_budget: int = 8 << 30, output_budget: int = 32 << 30, max_batch: int = 4096):
+        cfg = _ServerConfig(int(state_budget), int(output_budget), int(max_batch))
+        h = ctypes.c_void_p()
+        _check(lib().vmt_server_create(ctypes.byref(h), ctypes.byref(cfg)))
+        self._h = h
+
+    def submit(self, variant: str, lanes: int, dtype: str, seed: int, jump: int, n: int) -> int:
+        r = _Request(VARIANTS[variant], int(lanes), DTYPES[dtype], int(seed) & (2**64 - 1), int(jump) & (2**64 - 1),
+                     int(n))
+        rid = ctypes.c_uint64(0)
+        _check(lib().vmt_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, rid: int):
+        st, ptr, nb, lat = ctypes.c_int(), ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().vmt_server_poll(self._h, rid, ctypes.byref(st), ctypes.byref(ptr), ctypes.byref(nb),
+                                     ctypes.byref(lat)))
+        return st.value, ptr.value, nb.value, lat.value
+
+    def wait(self, rid: int, timeout_ms: int = 60000) -> int:
+        """0 when done; raises VMTError (VMT_ETIMEOUT, or the request's own error)."""
+        return _check(lib().vmt_server_wait(self._h, rid, int(timeout_ms)))
+
+    def copy(self, rid: int, dtype: str) -> np.ndarray:
+        st, ptr, nb, lat = self.poll(rid)
+        npdt = {"u32": np.uint32, "u64": np.uint64, "f32": np.float32, "f64": np.float64}[dtype]
+        out = np.empty(nb // np.dtype(npdt).itemsize, npdt)
+        _check(lib().vmt_server_copy(self._h, rid, _np_ptr(out), nb))
+        return out
+
+    def release(self, rid: int) -> None:
+        _check(lib().vmt_server_release(self._h, rid))
+
+    def stats(self) -> dict:
+        c = _Counters()
+        _check(lib().vmt_server_stats(self._h, ctypes.byref(c)))
+        return {n: getattr(c, n) for n, _ in _Counters._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vmt_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -82,53 +82,99 @@ __global__ void __launch_bounds__(SF_THREADS) gen_sfmt_kernel(GenArgs a)
     long long final_pos = p;
     uint32_t* out_u32 = (PLAIN_U32 && active) ? reinterpret_cast<uint32_t*>(em.elem0(0)) : nullptr;
 
-    if (__any_sync(FULL, p < B && total > 0)) {
-        const bool mine = p < B && total > 0;   // uniform unless RAGGED
-        const long long hi = mine ? min(B, p + total) : 0;
+    if constexpr (!RAGGED) {
+        // one position and one length for the whole launch: uniform loops
+        if (p < B && total > 0) {
+            const long long hi = min(B, p + total);
 #pragma unroll
-        for (int k = 0; k < SF_N; ++k) {
-            const long long f = 4LL * (static_cast<long long>(k) * M + t) + j;
-            const uint32_t partner = __shfl_down_sync(FULL, w[k], 1, 4);
-            if (!mine || !active) continue;
-            if (PLAIN_U32) {
-                if (f >= p && f < hi) __stcs(out_u32 + (f - p), w[k]);
-            } else {
-                sf_emit_generic(em, f, w[k], partner, p, hi, 0);
+            for (int k = 0; k < SF_N; ++k) {
+                const long long f = 4LL * (static_cast<long long>(k) * M + t) + j;
+                const uint32_t partner = __shfl_down_sync(FULL, w[k], 1, 4);
+                if (!active) continue;
+                if (PLAIN_U32) {
+                    if (f >= p && f < hi) __stcs(out_u32 + (f - p), w[k]);
+                } else {
+                    sf_emit_generic(em, f, w[k], partner, p, hi, 0);
+                }
             }
-        }
-        if (mine) {
             e = hi - p;
             final_pos = hi;
         }
-    }
-    while (__any_sync(FULL, e < total)) {
-        const bool live = e < total;
-        const long long hi = live ? min(B, total - e) : 0;
+        while (e < total) {
+            const long long hi = min(B, total - e);
 #pragma unroll
-        for (int k = 0; k < SF_N; ++k) {
-            const uint32_t wa = w[k];
-            const uint32_t wb = w[(k + SF_M) % SF_N];
-            const uint32_t wc = w[(k + SF_N - 2) % SF_N];
-            const uint32_t wd = w[(k + SF_N - 1) % SF_N];
-            uint32_t am1 = __shfl_up_sync(FULL, wa, 1, 4);
-            uint32_t cp1 = __shfl_down_sync(FULL, wc, 1, 4);
-            if (j == 0) am1 = 0u;
-            if (j == 3) cp1 = 0u;
-            const uint32_t nw = wa ^ __funnelshift_l(am1, wa, 8) ^ ((wb >> 11) & K) ^ __funnelshift_r(wc, cp1, 8) ^
-                                (wd << 18);
-            if (RAGGED) w[k] = live ? nw : wa;
-            else w[k] = nw;
-            const long long f = 4LL * (static_cast<long long>(k) * M + t) + j;
-            if (PLAIN_U32) {
-                if (active && live && f < hi) __stcs(out_u32 + e + f, nw);
-            } else {
-                const uint32_t partner = __shfl_down_sync(FULL, nw, 1, 4);
-                if (active && live) sf_emit_generic(em, f, nw, partner, 0, hi, e);
+            for (int k = 0; k < SF_N; ++k) {
+                const uint32_t wa = w[k];
+                const uint32_t wb = w[(k + SF_M) % SF_N];
+                const uint32_t wc = w[(k + SF_N - 2) % SF_N];
+                const uint32_t wd = w[(k + SF_N - 1) % SF_N];
+                uint32_t am1 = __shfl_up_sync(FULL, wa, 1, 4);
+                uint32_t cp1 = __shfl_down_sync(FULL, wc, 1, 4);
+                if (j == 0) am1 = 0u;
+                if (j == 3) cp1 = 0u;
+                const uint32_t nw = wa ^ __funnelshift_l(am1, wa, 8) ^ ((wb >> 11) & K) ^
+                                    __funnelshift_r(wc, cp1, 8) ^ (wd << 18);
+                w[k] = nw;
+                const long long f = 4LL * (static_cast<long long>(k) * M + t) + j;
+                if (PLAIN_U32) {
+                    if (active && f < hi) __stcs(out_u32 + e + f, nw);
+                } else {
+                    const uint32_t partner = __shfl_down_sync(FULL, nw, 1, 4);
+                    if (active) sf_emit_generic(em, f, nw, partner, 0, hi, e);
+                }
             }
-        }
-        if (live) {
             e += hi;
             final_pos = hi;
+        }
+    } else {
+        // lane-states of a warp differ in position or length
+        if (__any_sync(FULL, active && p < B && total > 0)) {
+            const bool mine = active && p < B && total > 0;
+            const long long hi = mine ? min(B, p + total) : 0;
+#pragma unroll
+            for (int k = 0; k < SF_N; ++k) {
+                const long long f = 4LL * (static_cast<long long>(k) * M + t) + j;
+                const uint32_t partner = __shfl_down_sync(FULL, w[k], 1, 4);
+                if (!mine) continue;
+                if (PLAIN_U32) {
+                    if (f >= p && f < hi) __stcs(out_u32 + (f - p), w[k]);
+                } else {
+                    sf_emit_generic(em, f, w[k], partner, p, hi, 0);
+                }
+            }
+            if (mine) {
+                e = hi - p;
+                final_pos = hi;
+            }
+        }
+        while (__any_sync(FULL, active && e < total)) {
+            const bool live = active && e < total;
+            const long long hi = live ? min(B, total - e) : 0;
+#pragma unroll
+            for (int k = 0; k < SF_N; ++k) {
+                const uint32_t wa = w[k];
+                const uint32_t wb = w[(k + SF_M) % SF_N];
+                const uint32_t wc = w[(k + SF_N - 2) % SF_N];
+                const uint32_t wd = w[(k + SF_N - 1) % SF_N];
+                uint32_t am1 = __shfl_up_sync(FULL, wa, 1, 4);
+                uint32_t cp1 = __shfl_down_sync(FULL, wc, 1, 4);
+                if (j == 0) am1 = 0u;
+                if (j == 3) cp1 = 0u;
+                const uint32_t nw = wa ^ __funnelshift_l(am1, wa, 8) ^ ((wb >> 11) & K) ^
+                                    __funnelshift_r(wc, cp1, 8) ^ (wd << 18);
+                w[k] = live ? nw : wa;   // a finished lane-state keeps its state
+                const long long f = 4LL * (static_cast<long long>(k) * M + t) + j;
+                if (PLAIN_U32) {
+                    if (live && f < hi) __stcs(out_u32 + e + f, nw);
+                } else {
+                    const uint32_t partner = __shfl_down_sync(FULL, nw, 1, 4);
+                    if (live) sf_emit_generic(em, f, nw, partner, 0, hi, e);
+                }
+            }
+            if (live) {
+                e += hi;
+                final_pos = hi;
+            }
         }
     }
     if (active) {

@@ -1,0 +1,481 @@
+// serve.cu -- request server for V-family generation (continuous batching).
+//
+// A request asks for n outputs of one fresh V-generator (variant, lanes M,
+// seed, jump offset d; Sec. 3 and 3.1).  The server keeps a FIFO of submitted
+// requests and a worker thread that, as long as memory allows, admits the
+// queue head into the next batch: its generator state (M * n_units words)
+// counts against the state budget until the batch has finished, its output
+// against the output budget until the client releases it.  A batch groups its
+// requests by kernel (variant, M, output type); per group one batched
+// initialisation (seeding, per-request jump offsets, lane de-phasing) runs on
+// the init stream and one persistent ragged generation (requests longest
+// first) on the generation stream, after the group's init.  Batches are
+// launched as soon as requests are admitted, so the initialisation of a new
+// batch (ALU-bound jumps) overlaps the generation of the previous one
+// (HBM-bound stores).  Completion is signalled from the stream by a host
+// function that stamps the requests' completion times.
+//
+// Failure handling, all on the host: a request that can never fit the budgets
+// or has invalid parameters fails alone (status < 0) and the server goes on;
+// vmt_server_wait gives up after its timeout with VMT_ETIMEOUT; destroying the
+// server waits for the batches in flight.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "vmt_internal.hpp"
+
+namespace {
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int words_per_out(int variant, int dtype)
+{
+    if (variant == VMT_MT19937_64) return 1;
+    return (dtype == VMT_U64 || dtype == VMT_F64) ? 2 : 1;
+}
+
+int out_bytes(int dtype) { return (dtype == VMT_U32 || dtype == VMT_F32) ? 4 : 8; }
+
+constexpr int kSlots = 4;          // batches that may be in flight at once
+constexpr int kMaxGroups = 16;     // kernels per batch
+
+struct Req {
+    vmt_request r{};
+    int status = VMT_SERVER_QUEUED;
+    void* out = nullptr;
+    int64_t bytes = 0;
+    int64_t state_bytes = 0;
+    bool admitted = false;   // its output bytes count against the budget
+    double t_submit = 0, t_done = 0;
+};
+
+struct Slot {
+    vmt::UnitDesc* h_units = nullptr;
+    vmt::UnitDesc* d_units = nullptr;
+    int* d_counter = nullptr;
+    uint64_t* h_seeds = nullptr;
+    uint64_t* h_jumps = nullptr;
+    bool busy = false;
+};
+
+struct Batch;
+struct HostDone {
+    vmt_server* srv;
+    Batch* b;
+};
+
+struct Batch {
+    int slot = -1;
+    std::vector<uint64_t> ids;
+    std::vector<vmt_state*> states;
+    int64_t state_bytes = 0;
+    std::atomic<bool> gpu_done{false};   // set by the stream's host function
+    double t_done = 0;
+    HostDone cb;
+};
+
+}  // namespace
+
+struct vmt_server {
+    vmt_server_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, Req> reqs;
+    std::deque<Batch*> inflight;
+    Slot slots[kSlots];
+    int64_t used_state = 0, used_out = 0, peak_state = 0, peak_out = 0;
+    int64_t batches = 0, completed = 0, failed = 0, bytes_out = 0;
+    uint64_t next_id = 1;
+    bool stop = false;
+    int device = 0;
+    cudaStream_t s_init = nullptr, s_gen = nullptr;
+    std::thread worker;
+};
+
+namespace {
+
+// Runs on the driver's callback thread once the batch's work is done.  It
+// takes no lock and makes no CUDA call: it stamps the time and raises a flag
+// that the worker picks up.
+void CUDART_CB on_batch_done(void* p)
+{
+    HostDone* h = static_cast<HostDone*>(p);
+    vmt_server* srv = h->srv;   // read before the flag: the worker may free the batch right after it
+    h->b->t_done = now_s();
+    h->b->gpu_done.store(true, std::memory_order_release);
+    srv->cv_work.notify_all();
+}
+
+// requests of one batch, grouped by kernel; returns the slot's unit count
+int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
+{
+    Slot& sl = s->slots[b->slot];
+    std::map<std::tuple<int, int, int>, std::vector<size_t>> groups;
+    for (size_t i = 0; i < rq.size(); ++i) groups[{rq[i]->r.variant, rq[i]->r.lanes, rq[i]->r.dtype}].push_back(i);
+    int64_t u0 = 0;
+    int gk = 0;
+    int rc = VMT_OK;
+    for (auto& kv : groups) {
+        const int variant = std::get<0>(kv.first), lanes = std::get<1>(kv.first), dtype = std::get<2>(kv.first);
+        const auto& idx = kv.second;
+        const int64_t k = static_cast<int64_t>(idx.size());
+        for (int64_t i = 0; i < k; ++i) {
+            sl.h_seeds[u0 + i] = rq[idx[static_cast<size_t>(i)]]->r.seed;
+            sl.h_jumps[u0 + i] = rq[idx[static_cast<size_t>(i)]]->r.jump;
+        }
+        vmt_state* st = nullptr;
+        rc = vmt::init_batch_impl(&st, variant, lanes, k, sl.h_seeds + u0, sl.h_jumps + u0, s->s_init, true);
+        if (rc) return rc;
+        b->states.push_back(st);
+        // outputs, then the ragged generation once this group's init is done
+        for (int64_t i = 0; i < k; ++i) {
+            Req* q = rq[idx[static_cast<size_t>(i)]];
+            if (cudaMallocAsync(&q->out, static_cast<size_t>(std::max<int64_t>(q->bytes, 16)), s->s_init) != cudaSuccess)
+                return VMT_ENOMEM;
+        }
+        cudaEvent_t ev;
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        cudaEventRecord(ev, s->s_init);
+        cudaStreamWaitEvent(s->s_gen, ev, 0);
+        cudaEventDestroy(ev);
+        const int64_t gen_bytes = vmt::state_bytes_per_gen(variant, lanes);
+        std::vector<std::pair<int64_t, int64_t>> order;   // (words, i)
+        for (int64_t i = 0; i < k; ++i) {
+            Req* q = rq[idx[static_cast<size_t>(i)]];
+            order.push_back({q->r.n * words_per_out(variant, dtype), i});
+        }
+        std::stable_sort(order.begin(), order.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+        int64_t nu = 0;
+        for (const auto& o : order) {
+            if (o.first == 0) continue;
+            vmt::UnitDesc& u = sl.h_units[u0 + nu++];
+            u.state = static_cast<char*>(st->d_states) + o.second * gen_bytes;
+            u.pos = st->d_pos + o.second;
+            u.total = o.first;
+            u.out = static_cast<char*>(rq[idx[static_cast<size_t>(o.second)]]->out);
+        }
+        if (nu) {
+            cudaMemcpyAsync(sl.d_units + u0, sl.h_units + u0, static_cast<size_t>(nu) * sizeof(vmt::UnitDesc),
+                            cudaMemcpyHostToDevice, s->s_gen);
+            rc = vmt::launch_unit_table(variant, lanes, dtype, sl.d_units + u0, nu, sl.d_counter + gk, s->s_gen);
+            if (rc) return rc;
+        }
+        u0 += k;
+        ++gk;
+    }
+    return VMT_OK;
+}
+
+// Finished batches leave the in-flight list; returns their states, to be
+// released after the lock is dropped (no CUDA call is made under the lock).
+std::vector<vmt_state*> retire(vmt_server* s)   // with s->mu held
+{
+    std::vector<vmt_state*> to_free;
+    while (!s->inflight.empty() && s->inflight.front()->gpu_done.load(std::memory_order_acquire)) {
+        Batch* b = s->inflight.front();
+        s->inflight.pop_front();
+        to_free.insert(to_free.end(), b->states.begin(), b->states.end());
+        s->used_state -= b->state_bytes;
+        for (uint64_t id : b->ids) {
+            auto it = s->reqs.find(id);
+            if (it == s->reqs.end()) continue;
+            if (it->second.status == VMT_SERVER_RUNNING) {
+                it->second.status = VMT_SERVER_DONE;
+                it->second.t_done = b->t_done;
+                ++s->completed;
+                s->bytes_out += it->second.bytes;
+            }
+        }
+        s->slots[b->slot].busy = false;
+        delete b;
+        s->cv_done.notify_all();
+    }
+    return to_free;
+}
+
+void worker_main(vmt_server* s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        std::vector<vmt_state*> to_free = retire(s);
+        if (!to_free.empty()) {
+            lk.unlock();
+            for (vmt_state* st : to_free) vmt::free_state_async(st, s->s_gen);
+            lk.lock();
+        }
+        if (s->stop && s->queue.empty() && s->inflight.empty()) break;
+        int slot = -1;
+        for (int i = 0; i < kSlots; ++i)
+            if (!s->slots[i].busy) {
+                slot = i;
+                break;
+            }
+        // admission: FIFO, as long as both budgets hold
+        std::vector<Req*> rq;
+        std::vector<uint64_t> ids;
+        std::map<std::tuple<int, int, int>, int> kinds;
+        int64_t add_state = 0;
+        while (slot >= 0 && !s->queue.empty() && static_cast<int>(rq.size()) < s->cfg.max_batch) {
+            const uint64_t id = s->queue.front();
+            Req& q = s->reqs[id];
+            if (q.state_bytes > s->cfg.state_budget_bytes || q.bytes > s->cfg.output_budget_bytes) {
+                q.status = VMT_ENOMEM;   // can never be admitted
+                ++s->failed;
+                s->queue.pop_front();
+                s->cv_done.notify_all();
+                continue;
+            }
+            if (s->used_state + add_state + q.state_bytes > s->cfg.state_budget_bytes ||
+                s->used_out + q.bytes > s->cfg.output_budget_bytes)
+                break;
+            const auto key = std::make_tuple(q.r.variant, q.r.lanes, q.r.dtype);
+            if (!kinds.count(key) && static_cast<int>(kinds.size()) == kMaxGroups) break;
+            kinds[key] = 1;
+            add_state += q.state_bytes;
+            s->used_out += q.bytes;
+            q.admitted = true;
+            q.status = VMT_SERVER_RUNNING;
+            rq.push_back(&q);
+            ids.push_back(id);
+            s->queue.pop_front();
+        }
+        if (rq.empty()) {
+            // nothing to launch: sleep until a submit, a release or a finished
+            // batch (the lock is released while waiting)
+            s->cv_work.wait_for(lk, std::chrono::microseconds(200));
+            continue;
+        }
+        s->used_state += add_state;
+        s->peak_state = std::max(s->peak_state, s->used_state);
+        s->peak_out = std::max(s->peak_out, s->used_out);
+        Batch* b = new Batch();
+        b->slot = slot;
+        b->ids = ids;
+        b->state_bytes = add_state;
+        b->cb = HostDone{s, b};
+        s->slots[slot].busy = true;
+        ++s->batches;
+        lk.unlock();
+        const int rc = launch_batch(s, b, rq);
+        cudaLaunchHostFunc(s->s_gen, on_batch_done, &b->cb);
+        lk.lock();
+        if (rc) {
+            for (uint64_t id : ids) {
+                Req& q = s->reqs[id];
+                q.status = rc;
+                ++s->failed;
+            }
+        }
+        s->inflight.push_back(b);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int vmt_server_create(vmt_server** out, const vmt_server_config* cfg)
+{
+    if (!out || !cfg) {
+        vmt::set_last_error("vmt_server_create: null argument");
+        return VMT_EINVAL;
+    }
+    if (cfg->max_batch < 1 || cfg->max_batch > 4096 || cfg->state_budget_bytes <= 0 || cfg->output_budget_bytes <= 0) {
+        vmt::set_last_error("vmt_server_create: max_batch must be in 1..4096 and budgets positive");
+        return VMT_EINVAL;
+    }
+    vmt_server* s = new vmt_server();
+    s->cfg = *cfg;
+    cudaGetDevice(&s->device);
+    bool ok = cudaStreamCreateWithFlags(&s->s_init, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&s->s_gen, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < kSlots && ok; ++i) {
+        Slot& sl = s->slots[i];
+        const size_t n = static_cast<size_t>(cfg->max_batch);
+        ok = cudaHostAlloc(reinterpret_cast<void**>(&sl.h_units), n * sizeof(vmt::UnitDesc), 0) == cudaSuccess &&
+             cudaMalloc(reinterpret_cast<void**>(&sl.d_units), n * sizeof(vmt::UnitDesc)) == cudaSuccess &&
+             cudaMalloc(reinterpret_cast<void**>(&sl.d_counter), kMaxGroups * sizeof(int)) == cudaSuccess &&
+             cudaHostAlloc(reinterpret_cast<void**>(&sl.h_seeds), n * 8, 0) == cudaSuccess &&
+             cudaHostAlloc(reinterpret_cast<void**>(&sl.h_jumps), n * 8, 0) == cudaSuccess;
+    }
+    if (!ok) {
+        vmt::set_last_error("vmt_server_create: CUDA resources could not be created");
+        vmt_server_destroy(s);
+        return VMT_ECUDA;
+    }
+    s->worker = std::thread(worker_main, s);
+    *out = s;
+    return VMT_OK;
+}
+
+int vmt_server_submit(vmt_server* s, const vmt_request* r, uint64_t* id)
+{
+    if (!s || !r || !id) {
+        vmt::set_last_error("vmt_server_submit: null argument");
+        return VMT_EINVAL;
+    }
+    const bool lanes_ok = r->lanes == 1 || r->lanes == 2 || r->lanes == 4 || r->lanes == 8 || r->lanes == 16;
+    if (r->variant < 0 || r->variant > 2 || !lanes_ok || r->dtype < VMT_U32 || r->dtype > VMT_F64 || r->n < 0 ||
+        (r->variant == VMT_MT19937_64 && r->dtype == VMT_U32) ||
+        r->n * words_per_out(r->variant, r->dtype) > (int64_t(1) << 30) ||
+        (words_per_out(r->variant, r->dtype) == 2 && r->lanes < 2)) {
+        vmt::set_last_error("vmt_server_submit: invalid request");
+        return VMT_EINVAL;
+    }
+    Req q;
+    q.r = *r;
+    q.bytes = r->n * out_bytes(r->dtype);
+    q.state_bytes = vmt::state_bytes_per_gen(r->variant, r->lanes) + 64;
+    q.t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        *id = s->next_id++;
+        s->reqs.emplace(*id, q);
+        s->queue.push_back(*id);
+    }
+    s->cv_work.notify_all();
+    return VMT_OK;
+}
+
+int vmt_server_poll(vmt_server* s, uint64_t id, int* status, void** out_dev, int64_t* bytes, double* latency_s)
+{
+    if (!s) return VMT_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) {
+        vmt::set_last_error("vmt_server_poll: unknown request id");
+        return VMT_EINVAL;
+    }
+    const Req& q = it->second;
+    if (status) *status = q.status;
+    if (out_dev) *out_dev = q.status == VMT_SERVER_DONE ? q.out : nullptr;
+    if (bytes) *bytes = q.bytes;
+    if (latency_s) *latency_s = q.status == VMT_SERVER_DONE ? q.t_done - q.t_submit : -1.0;
+    return VMT_OK;
+}
+
+int vmt_server_wait(vmt_server* s, uint64_t id, int timeout_ms)
+{
+    if (!s) return VMT_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+        auto it = s->reqs.find(id);
+        return it == s->reqs.end() || it->second.status == VMT_SERVER_DONE || it->second.status < 0;
+    });
+    if (!ok) {
+        vmt::set_last_error("vmt_server_wait: timed out");
+        return VMT_ETIMEOUT;
+    }
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return VMT_EINVAL;
+    return it->second.status < 0 ? it->second.status : VMT_OK;
+}
+
+int vmt_server_copy(vmt_server* s, uint64_t id, void* host_buf, int64_t cap)
+{
+    void* out = nullptr;
+    int64_t bytes = 0;
+    int status = 0;
+    const int rc = vmt_server_poll(s, id, &status, &out, &bytes, nullptr);
+    if (rc) return rc;
+    if (status != VMT_SERVER_DONE) {
+        vmt::set_last_error("vmt_server_copy: request not done");
+        return VMT_EBUSY;
+    }
+    if (!host_buf || cap < bytes) {
+        vmt::set_last_error("vmt_server_copy: host buffer too small");
+        return VMT_EINVAL;
+    }
+    if (bytes && cudaMemcpy(host_buf, out, static_cast<size_t>(bytes), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        vmt::set_last_error("vmt_server_copy: copy failed");
+        return VMT_ECUDA;
+    }
+    return VMT_OK;
+}
+
+int vmt_server_release(vmt_server* s, uint64_t id)
+{
+    if (!s) return VMT_EINVAL;
+    void* out = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(id);
+        if (it == s->reqs.end()) {
+            vmt::set_last_error("vmt_server_release: unknown request id");
+            return VMT_EINVAL;
+        }
+        Req& q = it->second;
+        if (q.status == VMT_SERVER_QUEUED || q.status == VMT_SERVER_RUNNING) {
+            vmt::set_last_error("vmt_server_release: request still pending");
+            return VMT_EBUSY;
+        }
+        out = q.out;
+        if (q.admitted) s->used_out -= q.bytes;
+        s->reqs.erase(it);
+    }
+    if (out) cudaFreeAsync(out, s->s_gen);
+    s->cv_work.notify_all();
+    return VMT_OK;
+}
+
+int vmt_server_stats(vmt_server* s, vmt_server_counters* out)
+{
+    if (!s || !out) return VMT_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->queued = static_cast<int64_t>(s->queue.size());
+    out->in_flight_batches = static_cast<int64_t>(s->inflight.size());
+    out->batches = s->batches;
+    out->completed = s->completed;
+    out->failed = s->failed;
+    out->bytes_out = s->bytes_out;
+    out->state_bytes_in_use = s->used_state;
+    out->output_bytes_in_use = s->used_out;
+    out->peak_state_bytes = s->peak_state;
+    out->peak_output_bytes = s->peak_out;
+    return VMT_OK;
+}
+
+void vmt_server_destroy(vmt_server* s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    if (s->s_gen) cudaStreamSynchronize(s->s_gen);
+    if (s->s_init) cudaStreamSynchronize(s->s_init);
+    for (auto& kv : s->reqs)
+        if (kv.second.out) cudaFreeAsync(kv.second.out, s->s_gen);
+    if (s->s_gen) cudaStreamSynchronize(s->s_gen);
+    for (auto& sl : s->slots) {
+        if (sl.h_units) cudaFreeHost(sl.h_units);
+        if (sl.d_units) cudaFree(sl.d_units);
+        if (sl.d_counter) cudaFree(sl.d_counter);
+        if (sl.h_seeds) cudaFreeHost(sl.h_seeds);
+        if (sl.h_jumps) cudaFreeHost(sl.h_jumps);
+    }
+    if (s->s_init) cudaStreamDestroy(s->s_init);
+    if (s->s_gen) cudaStreamDestroy(s->s_gen);
+    delete s;
+}
+
+}  // extern "C"

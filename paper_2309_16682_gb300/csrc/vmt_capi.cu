@@ -403,22 +403,7 @@ int ensure_digits(int variant)
 // ---------------------------------------------------------------------------
 // state object
 // ---------------------------------------------------------------------------
-struct vmt_state {
-    int variant = 0;
-    int lanes = 0;
-    int64_t count = 0;
-    std::vector<int64_t> h_pos;  // per generator: native words of its current block already emitted
-    bool uniform = true;         // all h_pos equal
-    int* d_pos = nullptr;        // device copy, read and written by the generation kernels
-    void* d_states = nullptr;    // [count][block words]
-    int device = 0;
-    // unit-launch scratch (ragged calls): pinned host staging and device copy
-    vmt::UnitDesc* h_units = nullptr;
-    vmt::UnitDesc* d_units = nullptr;
-    int* d_counter = nullptr;
-    int64_t units_cap = 0;
-    cudaEvent_t units_free = nullptr;   // recorded after the last upload of h_units
-};
+// struct vmt_state is defined in vmt_internal.hpp
 
 namespace {
 
@@ -506,10 +491,12 @@ int reserve_units(vmt::UnitDesc** h, vmt::UnitDesc** d, int** counter, int64_t* 
     return VMT_OK;
 }
 
-// one persistent unit launch: units already in d_units[0..n), counter slot k
-int launch_units(int variant, int lanes, int dtype, const vmt::UnitDesc* d_units, int64_t n, int* counter,
-                 cudaStream_t s)
+}  // namespace
+
+int vmt::launch_unit_table(int variant, int lanes, int dtype, const vmt::UnitDesc* d_units, int64_t n, int* counter,
+                           void* stream)
 {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n == 0) return VMT_OK;
     vmt::GenArgs a{};
     a.gens = n;
@@ -523,6 +510,14 @@ int launch_units(int variant, int lanes, int dtype, const vmt::UnitDesc* d_units
     CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
     CUDA_TRY(vmt::launch_generate(variant, lanes, a, true, s));
     return VMT_OK;
+}
+
+namespace {
+
+int launch_units(int variant, int lanes, int dtype, const vmt::UnitDesc* d_units, int64_t n, int* counter,
+                 cudaStream_t s)
+{
+    return vmt::launch_unit_table(variant, lanes, dtype, d_units, n, counter, s);
 }
 
 // Generate `nseg` consecutive segments for generators [g0, g0 + gens) of st,
@@ -689,8 +684,12 @@ int vmt_set_cache_dir(const char* path)
     return VMT_OK;
 }
 
-int vmt_init_batch(vmt_state** out, int variant, int lanes, int64_t count, const uint64_t* seeds,
-                   const uint64_t* jumps, void* cuda_stream)
+}  // extern "C"
+
+// Creates the state object; with async_alloc its device memory comes from
+// the stream-ordered pool of cuda_stream (free it with vmt::free_state_async).
+int vmt::init_batch_impl(vmt_state** out, int variant, int lanes, int64_t count, const uint64_t* seeds,
+                         const uint64_t* jumps, void* cuda_stream, bool async_alloc)
 {
     if (!out) return fail(VMT_EINVAL, "null output handle");
     *out = nullptr;
@@ -713,11 +712,20 @@ int vmt_init_batch(vmt_state** out, int variant, int lanes, int64_t count, const
     CUDA_TRY(cudaGetDevice(&st->device));
     const int64_t bytes = state_total_bytes(st.get());
     const int64_t B = vmt::block_words(variant, lanes);
-    if (cudaMalloc(&st->d_states, static_cast<size_t>(bytes)) != cudaSuccess ||
-        cudaMalloc(reinterpret_cast<void**>(&st->d_pos), static_cast<size_t>(count) * sizeof(int)) != cudaSuccess) {
+    bool ok;
+    if (async_alloc) {
+        ok = cudaMallocAsync(&st->d_states, static_cast<size_t>(bytes), s) == cudaSuccess &&
+             cudaMallocAsync(reinterpret_cast<void**>(&st->d_pos), static_cast<size_t>(count) * sizeof(int), s) ==
+                 cudaSuccess;
+        st->async_alloc = true;
+    } else {
+        ok = cudaMalloc(&st->d_states, static_cast<size_t>(bytes)) == cudaSuccess &&
+             cudaMalloc(reinterpret_cast<void**>(&st->d_pos), static_cast<size_t>(count) * sizeof(int)) == cudaSuccess;
+    }
+    if (!ok) {
         cudaGetLastError();
-        if (st->d_states) cudaFree(st->d_states);
-        return fail(VMT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " state bytes failed");
+        if (st->d_states) async_alloc ? (void)cudaFreeAsync(st->d_states, s) : (void)cudaFree(st->d_states);
+        return fail(VMT_ENOMEM, "allocation of " + std::to_string(bytes) + " state bytes failed");
     }
     st->h_pos.assign(static_cast<size_t>(count), B);   // exhausted: the first output twists
     st->uniform = true;
@@ -762,6 +770,25 @@ int vmt_init_batch(vmt_state** out, int variant, int lanes, int64_t count, const
     if (d_jumps) CUDA_TRY(cudaFreeAsync(d_jumps, s));
     *out = st.release();
     return VMT_OK;
+}
+
+void vmt::free_state_async(vmt_state* st, void* cuda_stream)
+{
+    if (!st) return;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (st->d_states) cudaFreeAsync(st->d_states, s);
+    if (st->d_pos) cudaFreeAsync(st->d_pos, s);
+    st->d_states = nullptr;
+    st->d_pos = nullptr;
+    vmt_free(st);
+}
+
+extern "C" {
+
+int vmt_init_batch(vmt_state** out, int variant, int lanes, int64_t count, const uint64_t* seeds,
+                   const uint64_t* jumps, void* cuda_stream)
+{
+    return vmt::init_batch_impl(out, variant, lanes, count, seeds, jumps, cuda_stream, false);
 }
 
 int vmt_init(vmt_state** st, int variant, int lanes, uint64_t seed, uint64_t jump, void* cuda_stream)
@@ -1257,8 +1284,15 @@ int vmt_device_status(int reset)
 void vmt_free(vmt_state* st)
 {
     if (!st) return;
-    if (st->d_states) cudaFree(st->d_states);
-    if (st->d_pos) cudaFree(st->d_pos);
+    if (st->async_alloc) {
+        // stream-ordered memory released without a stream: wait for the device
+        if (st->d_states || st->d_pos) cudaDeviceSynchronize();
+        if (st->d_states) cudaFreeAsync(st->d_states, nullptr);
+        if (st->d_pos) cudaFreeAsync(st->d_pos, nullptr);
+    } else {
+        if (st->d_states) cudaFree(st->d_states);
+        if (st->d_pos) cudaFree(st->d_pos);
+    }
     if (st->units_free) cudaEventSynchronize(st->units_free), cudaEventDestroy(st->units_free);
     if (st->h_units) cudaFreeHost(st->h_units);
     if (st->d_units) cudaFree(st->d_units);

@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/vmt.h"
 
 #define VMT_MAXSEG 4
@@ -93,6 +95,39 @@ cudaError_t launch_seed(int variant, long long count, const unsigned long long* 
 cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s);
 cudaError_t launch_jump_grid(int variant, const JumpGrid& gr, long long nitems, const uint32_t* polys, cudaStream_t s);
 cudaError_t launch_fill_int(int* p, long long n, int value, cudaStream_t s);
+
+}  // namespace vmt
+
+// A set of `count` V-generators (the public handle of include/vmt.h).
+struct vmt_state {
+    int variant = 0;
+    int lanes = 0;
+    int64_t count = 0;
+    std::vector<int64_t> h_pos;  // per generator: native words of its current block already emitted
+    bool uniform = true;         // all h_pos equal
+    int* d_pos = nullptr;        // device copy, read and written by the generation kernels
+    void* d_states = nullptr;    // [count][block words]
+    int device = 0;
+    bool async_alloc = false;    // device memory from a stream-ordered pool
+    // unit-launch scratch (ragged calls): pinned host staging and device copy
+    vmt::UnitDesc* h_units = nullptr;
+    vmt::UnitDesc* d_units = nullptr;
+    int* d_counter = nullptr;
+    int64_t units_cap = 0;
+    cudaEvent_t units_free = nullptr;   // recorded after the last upload of h_units
+};
+
+namespace vmt {
+
+// one persistent launch over a unit table already on the device; n units of
+// the given kernel, scheduled through counter (zeroed here)
+int launch_unit_table(int variant, int lanes, int dtype, const UnitDesc* d_units, int64_t n, int* counter,
+                      void* stream);
+
+// state creation with optional stream-ordered allocation, and its release
+int init_batch_impl(vmt_state** out, int variant, int lanes, int64_t count, const uint64_t* seeds,
+                    const uint64_t* jumps, void* cuda_stream, bool async_alloc);
+void free_state_async(vmt_state* st, void* cuda_stream);
 
 // tuned CTA size for a (variant, lanes) pair (0: the kernel's default)
 int tuned_threads(int variant, int lanes);

@@ -1,0 +1,120 @@
+"""The request server: every result is the same alone and in the mix, memory
+admission holds, and failures stay local (GPU).
+
+Failures are made on the host (an oversized request, an invalid one, a client
+that never releases its outputs); nothing here faults or stalls the GPU.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_16682_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vmt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_16682_gb300 as m
+    from paper_2309_16682_gb300 import build
+    build.build()
+    m.lib()
+    return m
+
+
+def _alone(vmt, variant, lanes, dtype, seed, jump, n):
+    g = vmt.VGenerator(variant, lanes, [seed], [jump])
+    t = g.generate(n, dtype)
+    if t.dtype == torch.uint32:
+        return t.cpu().view(torch.int32).numpy().view(np.uint32)[0]
+    if t.dtype == torch.uint64:
+        return t.cpu().view(torch.int64).numpy().view(np.uint64)[0]
+    return t.cpu().numpy()[0]
+
+
+def test_mix_equals_alone(vmt):
+    r = I.splitmix64(2024, 40 * 4).reshape(40, 4)
+    kinds = [("mt32", "u32"), ("mt32", "f32"), ("mt64", "u64"), ("mt64", "f64"), ("sfmt", "u32"), ("sfmt", "f64")]
+    sizes = [1, 2, 999, 10000, 123457, 624 * 16 + 3]
+    srv = vmt.Server(state_budget=1 << 30, output_budget=1 << 30, max_batch=64)
+    reqs = []
+    for i in range(40):
+        variant, dtype = kinds[int(r[i, 0] % np.uint64(len(kinds)))]
+        lanes = [2, 4, 8, 16][int(r[i, 1] % np.uint64(4))]
+        n = sizes[i % len(sizes)]
+        seed, jump = int(r[i, 2]), int(r[i, 3])
+        reqs.append((srv.submit(variant, lanes, dtype, seed, jump, n), variant, lanes, dtype, seed, jump, n))
+    for rid, variant, lanes, dtype, seed, jump, n in reqs:
+        srv.wait(rid)
+        got = srv.copy(rid, dtype)
+        ref = _alone(vmt, variant, lanes, dtype, seed, jump, n)
+        assert np.array_equal(got, ref), (variant, lanes, dtype, n)
+        st, ptr, nb, lat = srv.poll(rid)
+        assert st == vmt.SERVER_DONE and lat >= 0
+        srv.release(rid)
+    s = srv.stats()
+    assert s["completed"] == 40 and s["failed"] == 0 and s["output_bytes_in_use"] == 0
+    srv.close()
+
+
+def test_mix_matches_oracle_for_a_few(vmt, oracle_polys):
+    srv = vmt.Server(state_budget=1 << 28, output_budget=1 << 28, max_batch=8)
+    cases = [("mt32", 4, "u32", 11, 1 << 40, 5000), ("sfmt", 4, "u32", 12, 3, 3000), ("mt64", 8, "u64", 13, 77, 4000)]
+    ids = [srv.submit(*c) for c in cases]
+    for rid, (variant, lanes, dtype, seed, jump, n) in zip(ids, cases):
+        srv.wait(rid)
+        got = srv.copy(rid, dtype)
+        v = O.VARIANTS[variant]
+        ref = O.vstream(v, lanes, seed, n, dtype, d=jump)
+        assert np.array_equal(got, ref)
+        srv.release(rid)
+    srv.close()
+
+
+def test_admission_never_exceeds_budgets(vmt):
+    budget = 4 << 20
+    srv = vmt.Server(state_budget=1 << 30, output_budget=budget, max_batch=16)
+    ids = [srv.submit("mt32", 8, "u32", s, 0, 250_000) for s in range(12)]   # 1 MB each
+    for rid in ids:
+        srv.wait(rid)
+        srv.release(rid)
+    s = srv.stats()
+    assert s["completed"] == 12 and s["peak_output_bytes"] <= budget and s["output_bytes_in_use"] == 0
+    srv.close()
+
+
+def test_oversized_and_invalid_requests_fail_alone(vmt):
+    srv = vmt.Server(state_budget=1 << 30, output_budget=1 << 20, max_batch=16)
+    big = srv.submit("mt32", 4, "u32", 1, 0, 1_000_000)          # 4 MB > budget
+    ok = srv.submit("mt32", 4, "u32", 2, 0, 1000)
+    with pytest.raises(vmt.VMTError) as ei:
+        srv.wait(big)
+    assert ei.value.code == vmt.VMT_ENOMEM
+    srv.wait(ok)
+    srv.release(ok)
+    srv.release(big)
+    with pytest.raises(vmt.VMTError) as ei:
+        srv.submit("mt64", 4, "u32", 1, 0, 10)                     # u32 is not defined for MT19937-64
+    assert ei.value.code == vmt.VMT_EINVAL
+    srv.close()
+
+
+def test_stalled_consumer_blocks_admission_then_recovers(vmt):
+    srv = vmt.Server(state_budget=1 << 30, output_budget=(2 << 20) + 16, max_batch=16)
+    a = srv.submit("sfmt", 4, "u32", 1, 0, 262_144)   # 1 MiB each
+    b = srv.submit("sfmt", 4, "u32", 2, 0, 262_144)
+    c = srv.submit("sfmt", 4, "u32", 3, 0, 262_144)
+    srv.wait(a)
+    srv.wait(b)
+    with pytest.raises(vmt.VMTError) as ei:            # nobody released a or b yet
+        srv.wait(c, timeout_ms=300)
+    assert ei.value.code == vmt.VMT_ETIMEOUT
+    assert srv.poll(c)[0] == vmt.SERVER_QUEUED
+    srv.release(a)
+    srv.wait(c)
+    srv.release(b)
+    srv.release(c)
+    srv.close()
