@@ -250,6 +250,15 @@ __device__ __forceinline__ bool grid_item(const JumpGrid& gr, long long item, Ju
         it.dst = gr.states + g * gr.gen_bytes + static_cast<long long>(t) * gr.unit_bytes;
         it.dst_stride = gr.lanes;
         it.poly = t * 16 / gr.lanes;
+    } else if (gr.mode == JumpGrid::kChunk) {
+        const long long k = item / gr.lanes;
+        const int t = static_cast<int>(item % gr.lanes);
+        const int2 rc = gr.chunk_map[k];
+        it.src = gr.base + static_cast<long long>(rc.x) * gr.gen_bytes + static_cast<long long>(t) * gr.unit_bytes;
+        it.src_stride = gr.lanes;
+        it.dst = gr.states + k * gr.gen_bytes + static_cast<long long>(t) * gr.unit_bytes;
+        it.dst_stride = gr.lanes;
+        it.poly = gr.chunk_row0 + rc.y - 1;
     } else {
         const long long g = item;
         const int dig = static_cast<int>((gr.jumps[g] >> (8 * gr.digit)) & 255u);

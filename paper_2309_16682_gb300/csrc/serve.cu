@@ -51,8 +51,16 @@ int words_per_out(int variant, int dtype)
 
 int out_bytes(int dtype) { return (dtype == VMT_U32 || dtype == VMT_F32) ? 4 : 8; }
 
+// chunks of a request of w native words (the last one takes the rest)
+int64_t n_chunks(int variant, int lanes, int64_t w)
+{
+    const int64_t C = vmt::chunk_words(variant, lanes);
+    return std::min<int64_t>((w + C - 1) / C, vmt::kChunkRows + 1);
+}
+
 constexpr int kSlots = 4;          // batches that may be in flight at once
 constexpr int kMaxGroups = 16;     // kernels per batch
+constexpr int kMaxUnits = 65536;   // units (requests or chunks of requests) per batch
 
 struct Req {
     vmt_request r{};
@@ -60,16 +68,21 @@ struct Req {
     void* out = nullptr;
     int64_t bytes = 0;
     int64_t state_bytes = 0;
+    int64_t chunks = 1;      // generators it runs on (one per chunk)
     bool admitted = false;   // its output bytes count against the budget
+    cudaStream_t free_stream = nullptr;   // the stream its output was produced on
     double t_submit = 0, t_done = 0;
 };
 
 struct Slot {
+    cudaStream_t s_init = nullptr, s_gen = nullptr;   // this slot's batches run here
     vmt::UnitDesc* h_units = nullptr;
     vmt::UnitDesc* d_units = nullptr;
     int* d_counter = nullptr;
     uint64_t* h_seeds = nullptr;
     uint64_t* h_jumps = nullptr;
+    int2* h_map = nullptr;    // (request, chunk) of every chunk state
+    int2* d_map = nullptr;
     bool busy = false;
 };
 
@@ -104,7 +117,6 @@ struct vmt_server {
     uint64_t next_id = 1;
     bool stop = false;
     int device = 0;
-    cudaStream_t s_init = nullptr, s_gen = nullptr;
     std::thread worker;
 };
 
@@ -122,61 +134,103 @@ void CUDART_CB on_batch_done(void* p)
     srv->cv_work.notify_all();
 }
 
-// requests of one batch, grouped by kernel; returns the slot's unit count
+// Launch one batch.  Per kernel group: batched initialisation of the
+// requests' generators on the slot's init stream; requests longer than one
+// chunk (vmt::chunk_words) are cut at chunk boundaries, chunk c >= 1 getting
+// its own generator, the request's lanes advanced to S word c * chunk (one
+// device-side jump per lane); then one persistent ragged launch over all
+// chunks, longest first, on the slot's generation stream.
 int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
 {
     Slot& sl = s->slots[b->slot];
+    cudaStream_t s_init = sl.s_init, s_gen = sl.s_gen;
     std::map<std::tuple<int, int, int>, std::vector<size_t>> groups;
     for (size_t i = 0; i < rq.size(); ++i) groups[{rq[i]->r.variant, rq[i]->r.lanes, rq[i]->r.dtype}].push_back(i);
-    int64_t u0 = 0;
+    int64_t seed0 = 0, unit0 = 0, map0 = 0;
     int gk = 0;
     int rc = VMT_OK;
     for (auto& kv : groups) {
         const int variant = std::get<0>(kv.first), lanes = std::get<1>(kv.first), dtype = std::get<2>(kv.first);
         const auto& idx = kv.second;
         const int64_t k = static_cast<int64_t>(idx.size());
+        const int wpo = words_per_out(variant, dtype);
+        const int64_t C = vmt::chunk_words(variant, lanes);
         for (int64_t i = 0; i < k; ++i) {
-            sl.h_seeds[u0 + i] = rq[idx[static_cast<size_t>(i)]]->r.seed;
-            sl.h_jumps[u0 + i] = rq[idx[static_cast<size_t>(i)]]->r.jump;
+            sl.h_seeds[seed0 + i] = rq[idx[static_cast<size_t>(i)]]->r.seed;
+            sl.h_jumps[seed0 + i] = rq[idx[static_cast<size_t>(i)]]->r.jump;
         }
         vmt_state* st = nullptr;
-        rc = vmt::init_batch_impl(&st, variant, lanes, k, sl.h_seeds + u0, sl.h_jumps + u0, s->s_init, true);
+        rc = vmt::init_batch_impl(&st, variant, lanes, k, sl.h_seeds + seed0, sl.h_jumps + seed0, s_init, true);
         if (rc) return rc;
         b->states.push_back(st);
-        // outputs, then the ragged generation once this group's init is done
         for (int64_t i = 0; i < k; ++i) {
             Req* q = rq[idx[static_cast<size_t>(i)]];
-            if (cudaMallocAsync(&q->out, static_cast<size_t>(std::max<int64_t>(q->bytes, 16)), s->s_init) != cudaSuccess)
+            if (cudaMallocAsync(&q->out, static_cast<size_t>(std::max<int64_t>(q->bytes, 16)), s_init) != cudaSuccess)
                 return VMT_ENOMEM;
+            q->free_stream = s_gen;
+        }
+        // chunks: request i, chunk c in 1..P_i-1 (at most kChunkRows + 1 chunks)
+        int64_t nchunk = 0;
+        for (int64_t i = 0; i < k; ++i) {
+            const int64_t w = rq[idx[static_cast<size_t>(i)]]->r.n * wpo;
+            const int64_t P = n_chunks(variant, lanes, w);
+            for (int64_t c = 1; c < P; ++c) sl.h_map[map0 + nchunk++] = make_int2(static_cast<int>(i), static_cast<int>(c));
+        }
+        vmt_state* cst = nullptr;
+        if (nchunk) {
+            rc = vmt::alloc_states_async(&cst, variant, lanes, nchunk, s_init);
+            if (rc) return rc;
+            b->states.push_back(cst);
+            cudaMemcpyAsync(sl.d_map + map0, sl.h_map + map0, static_cast<size_t>(nchunk) * sizeof(int2),
+                            cudaMemcpyHostToDevice, s_init);
+            rc = vmt::launch_chunk_jumps(st, cst, sl.d_map + map0, s_init);
+            if (rc) return rc;
         }
         cudaEvent_t ev;
         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        cudaEventRecord(ev, s->s_init);
-        cudaStreamWaitEvent(s->s_gen, ev, 0);
+        cudaEventRecord(ev, s_init);
+        cudaStreamWaitEvent(s_gen, ev, 0);
         cudaEventDestroy(ev);
+        // units: chunk 0 of every request on its own generator, chunks >= 1 on
+        // the chunk generators; the last chunk takes the rest of the request
         const int64_t gen_bytes = vmt::state_bytes_per_gen(variant, lanes);
-        std::vector<std::pair<int64_t, int64_t>> order;   // (words, i)
+        const int eb = out_bytes(dtype);
+        std::vector<vmt::UnitDesc> units;
+        int64_t ck = 0;
         for (int64_t i = 0; i < k; ++i) {
             Req* q = rq[idx[static_cast<size_t>(i)]];
-            order.push_back({q->r.n * words_per_out(variant, dtype), i});
+            const int64_t w = q->r.n * wpo;
+            if (w == 0) continue;
+            const int64_t P = n_chunks(variant, lanes, w);
+            for (int64_t c = 0; c < P; ++c) {
+                vmt::UnitDesc u{};
+                const int64_t w0 = c * C, w1 = (c == P - 1) ? w : (c + 1) * C;
+                if (c == 0) {
+                    u.state = static_cast<char*>(st->d_states) + i * gen_bytes;
+                    u.pos = st->d_pos + i;
+                } else {
+                    u.state = static_cast<char*>(cst->d_states) + ck * gen_bytes;
+                    u.pos = cst->d_pos + ck;
+                    ++ck;
+                }
+                u.total = w1 - w0;
+                u.out = static_cast<char*>(q->out) + (w0 / wpo) * eb;
+                units.push_back(u);
+            }
         }
-        std::stable_sort(order.begin(), order.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-        int64_t nu = 0;
-        for (const auto& o : order) {
-            if (o.first == 0) continue;
-            vmt::UnitDesc& u = sl.h_units[u0 + nu++];
-            u.state = static_cast<char*>(st->d_states) + o.second * gen_bytes;
-            u.pos = st->d_pos + o.second;
-            u.total = o.first;
-            u.out = static_cast<char*>(rq[idx[static_cast<size_t>(o.second)]]->out);
-        }
+        std::stable_sort(units.begin(), units.end(),
+                         [](const vmt::UnitDesc& x, const vmt::UnitDesc& y) { return x.total > y.total; });
+        const int64_t nu = static_cast<int64_t>(units.size());
         if (nu) {
-            cudaMemcpyAsync(sl.d_units + u0, sl.h_units + u0, static_cast<size_t>(nu) * sizeof(vmt::UnitDesc),
-                            cudaMemcpyHostToDevice, s->s_gen);
-            rc = vmt::launch_unit_table(variant, lanes, dtype, sl.d_units + u0, nu, sl.d_counter + gk, s->s_gen);
+            std::memcpy(sl.h_units + unit0, units.data(), static_cast<size_t>(nu) * sizeof(vmt::UnitDesc));
+            cudaMemcpyAsync(sl.d_units + unit0, sl.h_units + unit0, static_cast<size_t>(nu) * sizeof(vmt::UnitDesc),
+                            cudaMemcpyHostToDevice, s_gen);
+            rc = vmt::launch_unit_table(variant, lanes, dtype, sl.d_units + unit0, nu, sl.d_counter + gk, s_gen);
             if (rc) return rc;
         }
-        u0 += k;
+        seed0 += k;
+        unit0 += nu;
+        map0 += nchunk;
         ++gk;
     }
     return VMT_OK;
@@ -184,13 +238,17 @@ int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
 
 // Finished batches leave the in-flight list; returns their states, to be
 // released after the lock is dropped (no CUDA call is made under the lock).
-std::vector<vmt_state*> retire(vmt_server* s)   // with s->mu held
+std::vector<std::pair<vmt_state*, cudaStream_t>> retire(vmt_server* s)   // with s->mu held
 {
-    std::vector<vmt_state*> to_free;
-    while (!s->inflight.empty() && s->inflight.front()->gpu_done.load(std::memory_order_acquire)) {
-        Batch* b = s->inflight.front();
-        s->inflight.pop_front();
-        to_free.insert(to_free.end(), b->states.begin(), b->states.end());
+    std::vector<std::pair<vmt_state*, cudaStream_t>> to_free;
+    for (size_t i = 0; i < s->inflight.size();) {
+        Batch* b = s->inflight[i];
+        if (!b->gpu_done.load(std::memory_order_acquire)) {
+            ++i;
+            continue;
+        }
+        s->inflight.erase(s->inflight.begin() + static_cast<std::ptrdiff_t>(i));
+        for (vmt_state* st : b->states) to_free.push_back({st, s->slots[b->slot].s_gen});
         s->used_state -= b->state_bytes;
         for (uint64_t id : b->ids) {
             auto it = s->reqs.find(id);
@@ -214,10 +272,10 @@ void worker_main(vmt_server* s)
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
-        std::vector<vmt_state*> to_free = retire(s);
+        const auto to_free = retire(s);
         if (!to_free.empty()) {
             lk.unlock();
-            for (vmt_state* st : to_free) vmt::free_state_async(st, s->s_gen);
+            for (const auto& f : to_free) vmt::free_state_async(f.first, f.second);
             lk.lock();
         }
         if (s->stop && s->queue.empty() && s->inflight.empty()) break;
@@ -231,7 +289,7 @@ void worker_main(vmt_server* s)
         std::vector<Req*> rq;
         std::vector<uint64_t> ids;
         std::map<std::tuple<int, int, int>, int> kinds;
-        int64_t add_state = 0;
+        int64_t add_state = 0, units = 0;
         while (slot >= 0 && !s->queue.empty() && static_cast<int>(rq.size()) < s->cfg.max_batch) {
             const uint64_t id = s->queue.front();
             Req& q = s->reqs[id];
@@ -247,6 +305,8 @@ void worker_main(vmt_server* s)
                 break;
             const auto key = std::make_tuple(q.r.variant, q.r.lanes, q.r.dtype);
             if (!kinds.count(key) && static_cast<int>(kinds.size()) == kMaxGroups) break;
+            if (units + q.chunks > kMaxUnits) break;
+            units += q.chunks;
             kinds[key] = 1;
             add_state += q.state_bytes;
             s->used_out += q.bytes;
@@ -274,7 +334,7 @@ void worker_main(vmt_server* s)
         ++s->batches;
         lk.unlock();
         const int rc = launch_batch(s, b, rq);
-        cudaLaunchHostFunc(s->s_gen, on_batch_done, &b->cb);
+        cudaLaunchHostFunc(s->slots[slot].s_gen, on_batch_done, &b->cb);
         lk.lock();
         if (rc) {
             for (uint64_t id : ids) {
@@ -304,13 +364,17 @@ int vmt_server_create(vmt_server** out, const vmt_server_config* cfg)
     vmt_server* s = new vmt_server();
     s->cfg = *cfg;
     cudaGetDevice(&s->device);
-    bool ok = cudaStreamCreateWithFlags(&s->s_init, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&s->s_gen, cudaStreamNonBlocking) == cudaSuccess;
+    bool ok = true;
     for (int i = 0; i < kSlots && ok; ++i) {
         Slot& sl = s->slots[i];
         const size_t n = static_cast<size_t>(cfg->max_batch);
-        ok = cudaHostAlloc(reinterpret_cast<void**>(&sl.h_units), n * sizeof(vmt::UnitDesc), 0) == cudaSuccess &&
-             cudaMalloc(reinterpret_cast<void**>(&sl.d_units), n * sizeof(vmt::UnitDesc)) == cudaSuccess &&
+        const size_t nu = static_cast<size_t>(kMaxUnits);
+        ok = cudaStreamCreateWithFlags(&sl.s_init, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&sl.s_gen, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaHostAlloc(reinterpret_cast<void**>(&sl.h_units), nu * sizeof(vmt::UnitDesc), 0) == cudaSuccess &&
+             cudaMalloc(reinterpret_cast<void**>(&sl.d_units), nu * sizeof(vmt::UnitDesc)) == cudaSuccess &&
+             cudaHostAlloc(reinterpret_cast<void**>(&sl.h_map), nu * sizeof(int2), 0) == cudaSuccess &&
+             cudaMalloc(reinterpret_cast<void**>(&sl.d_map), nu * sizeof(int2)) == cudaSuccess &&
              cudaMalloc(reinterpret_cast<void**>(&sl.d_counter), kMaxGroups * sizeof(int)) == cudaSuccess &&
              cudaHostAlloc(reinterpret_cast<void**>(&sl.h_seeds), n * 8, 0) == cudaSuccess &&
              cudaHostAlloc(reinterpret_cast<void**>(&sl.h_jumps), n * 8, 0) == cudaSuccess;
@@ -342,7 +406,8 @@ int vmt_server_submit(vmt_server* s, const vmt_request* r, uint64_t* id)
     Req q;
     q.r = *r;
     q.bytes = r->n * out_bytes(r->dtype);
-    q.state_bytes = vmt::state_bytes_per_gen(r->variant, r->lanes) + 64;
+    q.chunks = std::max<int64_t>(n_chunks(r->variant, r->lanes, r->n * words_per_out(r->variant, r->dtype)), 1);
+    q.state_bytes = q.chunks * (vmt::state_bytes_per_gen(r->variant, r->lanes) + 64);
     q.t_submit = now_s();
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -414,6 +479,7 @@ int vmt_server_release(vmt_server* s, uint64_t id)
 {
     if (!s) return VMT_EINVAL;
     void* out = nullptr;
+    cudaStream_t fs = nullptr;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         auto it = s->reqs.find(id);
@@ -427,10 +493,11 @@ int vmt_server_release(vmt_server* s, uint64_t id)
             return VMT_EBUSY;
         }
         out = q.out;
+        fs = q.free_stream;
         if (q.admitted) s->used_out -= q.bytes;
         s->reqs.erase(it);
     }
-    if (out) cudaFreeAsync(out, s->s_gen);
+    if (out) cudaFreeAsync(out, fs);
     s->cv_work.notify_all();
     return VMT_OK;
 }
@@ -461,20 +528,24 @@ void vmt_server_destroy(vmt_server* s)
     }
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
-    if (s->s_gen) cudaStreamSynchronize(s->s_gen);
-    if (s->s_init) cudaStreamSynchronize(s->s_init);
-    for (auto& kv : s->reqs)
-        if (kv.second.out) cudaFreeAsync(kv.second.out, s->s_gen);
-    if (s->s_gen) cudaStreamSynchronize(s->s_gen);
     for (auto& sl : s->slots) {
+        if (sl.s_gen) cudaStreamSynchronize(sl.s_gen);
+        if (sl.s_init) cudaStreamSynchronize(sl.s_init);
+    }
+    for (auto& kv : s->reqs)
+        if (kv.second.out) cudaFreeAsync(kv.second.out, kv.second.free_stream);
+    for (auto& sl : s->slots) {
+        if (sl.s_gen) cudaStreamSynchronize(sl.s_gen);
         if (sl.h_units) cudaFreeHost(sl.h_units);
         if (sl.d_units) cudaFree(sl.d_units);
         if (sl.d_counter) cudaFree(sl.d_counter);
         if (sl.h_seeds) cudaFreeHost(sl.h_seeds);
         if (sl.h_jumps) cudaFreeHost(sl.h_jumps);
+        if (sl.h_map) cudaFreeHost(sl.h_map);
+        if (sl.d_map) cudaFree(sl.d_map);
+        if (sl.s_init) cudaStreamDestroy(sl.s_init);
+        if (sl.s_gen) cudaStreamDestroy(sl.s_gen);
     }
-    if (s->s_init) cudaStreamDestroy(s->s_init);
-    if (s->s_gen) cudaStreamDestroy(s->s_gen);
     delete s;
 }
 

@@ -126,6 +126,7 @@ int log2i(int m)
 constexpr int kPeriodExp = 19937;
 constexpr int kLaneRowQ = kPeriodExp - 4;   // J for M = 16
 constexpr int kDigitRows = 8 * 255;
+constexpr int kChunkRow0 = 16 + kDigitRows;   // first chunk row (chunk 1)
 constexpr int kChainLo = 72;                // x^(2^q), q < 72, kept for d-jumps
 constexpr int kChainHiFrom = kPeriodExp - 8;
 
@@ -133,6 +134,7 @@ struct VariantCtx {
     std::mutex mu_lock;
     bool ready = false;
     bool digits_ready = false;
+    bool chunks_ready = false;
     std::unique_ptr<vmt::gf2::Modulus> mod;
     std::vector<Poly> chain_lo;    // q = 0 .. kChainLo-1
     std::vector<Poly> chain_hi;    // q = kChainHiFrom .. kPeriodExp
@@ -346,7 +348,7 @@ int ensure_variant(int variant, cudaStream_t st)
         c.device = -1;
     }
     if (c.device != dev) {
-        const size_t rows = 16 + kDigitRows;
+        const size_t rows = 16 + kDigitRows + vmt::kChunkRows;
         if (c.d_table) cudaFree(c.d_table);
         c.d_table = nullptr;
         CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&c.d_table), rows * vmt::kPolyWords * sizeof(uint32_t)));
@@ -363,7 +365,30 @@ int ensure_variant(int variant, cudaStream_t st)
         CUDA_TRY(cudaMemcpy(c.d_row_deg, c.row_deg.data(), rows * sizeof(int), cudaMemcpyHostToDevice));
         c.device = dev;
         c.digits_ready = false;
+        c.chunks_ready = false;
     }
+    return VMT_OK;
+}
+
+// rows x^(c * kChunkBlocks * n) for chunks c = 1..kChunkRows
+int ensure_chunks(int variant)
+{
+    VariantCtx& c = g_ctx[variant];
+    std::lock_guard<std::mutex> lk(c.mu_lock);
+    if (c.chunks_ready) return VMT_OK;
+    const uint64_t delta = static_cast<uint64_t>(vmt::kChunkBlocks) * vmt::units_per_lane(variant);
+    std::vector<uint32_t> host(static_cast<size_t>(vmt::kChunkRows) * vmt::kPolyWords);
+    const Poly step = c.mod->x_pow(delta);
+    Poly cur = step;
+    for (int j = 1; j <= vmt::kChunkRows; ++j) {
+        if (j > 1) cur = c.mod->mul(cur, step);
+        to_rows(cur, &host[static_cast<size_t>(j - 1) * vmt::kPolyWords]);
+        c.row_deg[static_cast<size_t>(kChunkRow0 + j - 1)] = vmt::gf2::degree(cur);
+    }
+    CUDA_TRY(cudaMemcpy(c.d_table + static_cast<size_t>(kChunkRow0) * vmt::kPolyWords, host.data(),
+                        host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c.d_row_deg, c.row_deg.data(), c.row_deg.size() * sizeof(int), cudaMemcpyHostToDevice));
+    c.chunks_ready = true;
     return VMT_OK;
 }
 
@@ -770,6 +795,48 @@ int vmt::init_batch_impl(vmt_state** out, int variant, int lanes, int64_t count,
     if (d_jumps) CUDA_TRY(cudaFreeAsync(d_jumps, s));
     *out = st.release();
     return VMT_OK;
+}
+
+int vmt::alloc_states_async(vmt_state** out, int variant, int lanes, int64_t count, void* cuda_stream)
+{
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    std::unique_ptr<vmt_state> st(new vmt_state());
+    st->variant = variant;
+    st->lanes = lanes;
+    st->count = count;
+    st->async_alloc = true;
+    CUDA_TRY(cudaGetDevice(&st->device));
+    const int64_t B = vmt::block_words(variant, lanes);
+    if (cudaMallocAsync(&st->d_states, static_cast<size_t>(state_total_bytes(st.get())), s) != cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void**>(&st->d_pos), static_cast<size_t>(count) * sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        if (st->d_states) cudaFreeAsync(st->d_states, s);
+        return fail(VMT_ENOMEM, "chunk state allocation failed");
+    }
+    st->h_pos.assign(static_cast<size_t>(count), B);
+    CUDA_TRY(vmt::launch_fill_int(st->d_pos, count, static_cast<int>(B), s));
+    *out = st.release();
+    return VMT_OK;
+}
+
+int vmt::launch_chunk_jumps(const vmt_state* requests, vmt_state* chunks, const int2* d_map, void* cuda_stream)
+{
+    const int variant = requests->variant;
+    int rc = ensure_chunks(variant);
+    if (rc) return rc;
+    VariantCtx& c = g_ctx[variant];
+    vmt::JumpGrid gr{};
+    gr.mode = vmt::JumpGrid::kChunk;
+    gr.count = chunks->count;
+    gr.lanes = requests->lanes;
+    gr.base = static_cast<char*>(requests->d_states);
+    gr.unit_bytes = vmt::word_bytes(variant) * vmt::words_per_unit(variant);
+    gr.states = static_cast<char*>(chunks->d_states);
+    gr.gen_bytes = vmt::state_bytes_per_gen(variant, requests->lanes);
+    gr.row_deg = c.d_row_deg;
+    gr.chunk_map = d_map;
+    gr.chunk_row0 = kChunkRow0;
+    return run_jump_grid(variant, gr, chunks->count * requests->lanes, c.d_table, static_cast<cudaStream_t>(cuda_stream));
 }
 
 void vmt::free_state_async(vmt_state* st, void* cuda_stream)

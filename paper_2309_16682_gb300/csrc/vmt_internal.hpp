@@ -75,8 +75,11 @@ constexpr int kPolyWords = 640;  // u32 words per polynomial row (20480 bits)
 //            row t*16/lanes applied to g's base state (unit-major base);
 //   kDigit:  item g applies row 16 + 255*digit + d - 1 in place to g's base
 //            state, d = byte `digit` of jumps[g] (nothing when d = 0).
+//   kChunk:  item k*lanes + t writes lane t of chunk state k (X-hat layout in
+//            `states`) as row chunk_row0 + c - 1 applied to lane t of request r's
+//            X-hat (in `base`, X-hat layout), (r, c) = chunk_map[k].
 struct JumpGrid {
-    enum { kFanOut = 1, kDigit = 2 };
+    enum { kFanOut = 1, kDigit = 2, kChunk = 3 };
     int mode;
     long long count;
     int lanes;
@@ -87,7 +90,17 @@ struct JumpGrid {
     const unsigned long long* jumps;
     int digit;
     const int* row_deg;
+    const int2* chunk_map;
+    int chunk_row0;
 };
+
+// Chunks of one long stream: chunk c starts at S word c * chunk_words(...)
+// (a whole number of blocks), so its lanes are the stream's lanes advanced by
+// c * kChunkBlocks * n steps.  Rows for c = 1 .. kChunkRows of that jump are
+// kept per variant.
+constexpr int kChunkBlocks = 1024;
+constexpr int kChunkRows = 255;
+inline int64_t chunk_words(int variant, int lanes) { return static_cast<int64_t>(kChunkBlocks) * block_words(variant, lanes); }
 
 // ragged: generators of one launch may differ in position or length
 cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, bool ragged, cudaStream_t s);
@@ -128,6 +141,14 @@ int launch_unit_table(int variant, int lanes, int dtype, const UnitDesc* d_units
 int init_batch_impl(vmt_state** out, int variant, int lanes, int64_t count, const uint64_t* seeds,
                     const uint64_t* jumps, void* cuda_stream, bool async_alloc);
 void free_state_async(vmt_state* st, void* cuda_stream);
+
+// `count` generators with unset states (to be written by a jump), fresh
+// positions, stream-ordered memory
+int alloc_states_async(vmt_state** out, int variant, int lanes, int64_t count, void* cuda_stream);
+
+// chunk states: chunk k = row (chunk_map[k].y) applied to every lane of
+// request chunk_map[k].x of `requests`; d_map on the device
+int launch_chunk_jumps(const vmt_state* requests, vmt_state* chunks, const int2* d_map, void* cuda_stream);
 
 // tuned CTA size for a (variant, lanes) pair (0: the kernel's default)
 int tuned_threads(int variant, int lanes);

@@ -118,3 +118,35 @@ def test_stalled_consumer_blocks_admission_then_recovers(vmt):
     srv.release(b)
     srv.release(c)
     srv.close()
+
+
+def test_long_requests_split_into_chunks_equal_alone(vmt):
+    # requests longer than one chunk run as several generators, chunk c's
+    # lanes jumped to the chunk's first word; the stream must not change
+    srv = vmt.Server(state_budget=1 << 30, output_budget=1 << 30, max_batch=16)
+    cases = [("mt32", 4, "u32", 31, 0, 3_000_000),        # 2 chunks
+             ("mt32", 1, "f32", 32, 5, 5_000_000),        # 8 chunks, ragged tail
+             ("mt64", 4, "f64", 33, 1 << 33, 3_000_000),  # 3 chunks
+             ("sfmt", 2, "f64", 34, 9, 2_000_000),        # 4 chunks of 32-bit word pairs
+             ("mt32", 2, "u32", 35, 0, 1000)]             # short one in the same batch
+    ids = [srv.submit(*c) for c in cases]
+    for rid, c in zip(ids, cases):
+        srv.wait(rid)
+        got = srv.copy(rid, c[2])
+        assert np.array_equal(got, _alone(vmt, *c)), c
+        srv.release(rid)
+    srv.close()
+
+
+def test_chunk_boundary_matches_oracle(vmt, oracle_polys):
+    # the words on both sides of the first chunk boundary, against the oracle
+    lanes = 4
+    C = 1024 * lanes * 624
+    srv = vmt.Server(state_budget=1 << 28, output_budget=1 << 28, max_batch=4)
+    rid = srv.submit("mt32", lanes, "u32", 41, 3, C + 700)
+    srv.wait(rid)
+    got = srv.copy(rid, "u32")
+    ref = O.vstream(O.VARIANTS["mt32"], lanes, 41, 1400, "u32", start_word=C - 700, d=3)
+    assert np.array_equal(got[C - 700:], ref)
+    srv.release(rid)
+    srv.close()
