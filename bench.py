@@ -240,13 +240,14 @@ def run_served(vmt, requests: int, rate: float, plain_requests: int):
              int(tr["seed"][i]), int(tr["jump"][i]), int(tr["n"][i]), float(tr["arrival_s"][i]))
             for i in range(requests)]
     esize = {"u32": 4, "u64": 8}
-    srv = vmt.Server(state_budget=16 << 30, output_budget=96 << 30, max_batch=4096)
+    srv = vmt.Server(state_budget=16 << 30, output_budget=96 << 30, max_batch=4096, reserve=True)
     # warm-up: polynomial tables of every variant and digit tables
     for v in ("mt32", "mt64", "sfmt"):
         rid = srv.submit(v, 4, native[{"mt32": 0, "mt64": 1, "sfmt": 2}[v]], 1, 12345, 1000)
         srv.wait(rid)
         srv.release(rid)
     torch.cuda.synchronize()
+    warm_stats = srv.stats()
     import threading as th
     ids = [None] * requests
     lat = [0.0] * requests
@@ -271,11 +272,15 @@ def run_served(vmt, requests: int, rate: float, plain_requests: int):
     rt.join()
     t_end = max(done_at)
     stats = srv.stats()
+    stats0 = warm_stats
     srv.close()
     total_bytes = sum(n * esize[dt] for (_, _, dt, _, _, n, _) in reqs)
     batched = {"p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99),
                "throughput_GBps": total_bytes / (t_end - t0) / 1e9, "batches": stats["batches"],
-               "peak_output_bytes": stats["peak_output_bytes"], "wall_s": t_end - t0}
+               "peak_output_bytes": stats["peak_output_bytes"], "wall_s": t_end - t0,
+               "host_launch_s": stats["host_launch_s"] - stats0["host_launch_s"],
+               "init_gpu_s": stats["init_gpu_s"] - stats0["init_gpu_s"],
+               "batch_gpu_s": stats["batch_gpu_s"] - stats0["batch_gpu_s"]}
     # plain form on the first plain_requests requests of the same trace
     pr = reqs[:plain_requests]
     plat = []

@@ -107,6 +107,18 @@ int vmt_jump(vmt_state* st, const uint64_t* poly, int64_t nbits, void* cuda_stre
 int vmt_jump_poly(int variant, uint64_t d, int log2_extra, uint64_t* poly_out, int64_t cap_words);
 
 /*
+ * vmt_prepare -- build, for the current device, every table the variant's
+ * initialisation and jumps use: the characteristic polynomial (Sec. 3.2,
+ * found by Berlekamp-Massey or read from the cache directory), the chain
+ * x^(2^q) mod it, the base-256 digit rows x^(v 256^i) of 64-bit jump offsets
+ * and the rows x^(c * 1024 * n) that cut long server requests into chunks.
+ * Every other entry point builds what it needs on first use; calling this
+ * first moves that one-time cost (up to seconds) out of the first request.
+ * Returns VMT_EINVAL for a bad variant.
+ */
+int vmt_prepare(int variant, void* cuda_stream);
+
+/*
  * vmt_generate -- the next n outputs of type dtype from every generator.
  * Generator g writes out_dev[g*n .. g*n + n) (device memory, caller-owned,
  * at least count*n elements).  The stream continues across calls: a call
@@ -176,6 +188,16 @@ void vmt_batch_destroy(vmt_batch* b);
  *                       has finished) and returns its bytes to the budget
  * Limits: n * words-per-output <= 2^30; u64/f64 from 32-bit generators need
  * lanes >= 2.  A request larger than a budget fails with VMT_ENOMEM.
+ * Memory: states and outputs come from a stream-ordered pool owned by the
+ * server that keeps up to both budgets' bytes between requests; with
+ * reserve != 0 the pool takes that memory at creation (creation fails with
+ * VMT_ENOMEM if the device cannot hold it), so admitted requests never wait
+ * for the driver to map memory, and every variant's tables are prepared
+ * (vmt_prepare) before the server accepts requests.
+ * Counters: host_launch_s is the worker's host time spent issuing batches;
+ * init_gpu_s sums, over finished batches, the device time from the start of
+ * a batch's initialisation to its end (seeding, jumps, chunk jumps);
+ * batch_gpu_s the device time from that start to the end of its generation.
  */
 #define VMT_SERVER_QUEUED 0
 #define VMT_SERVER_RUNNING 1
@@ -186,6 +208,7 @@ typedef struct {
     int64_t state_budget_bytes;
     int64_t output_budget_bytes;
     int max_batch;
+    int reserve;   /* nonzero: map both budgets into the server's pool at creation */
 } vmt_server_config;
 typedef struct {
     int variant, lanes, dtype;
@@ -195,6 +218,7 @@ typedef struct {
 typedef struct {
     int64_t queued, in_flight_batches, batches, completed, failed, bytes_out;
     int64_t state_bytes_in_use, output_bytes_in_use, peak_state_bytes, peak_output_bytes;
+    double host_launch_s, init_gpu_s, batch_gpu_s;
 } vmt_server_counters;
 
 int vmt_server_create(vmt_server** s, const vmt_server_config* cfg);
@@ -254,6 +278,18 @@ int vmt_device_status(int reset);
  */
 int vmt_tune_set(int variant, int lanes, int threads);
 int vmt_tune_get(int variant, int lanes);
+
+/*
+ * vmt_tune_jump_set / vmt_tune_jump_get -- jump launches (initialisation,
+ * vmt_jump, server chunks) with fewer lane-jumps than split_below give each
+ * lane-jump a whole CTA, whose warps share the work of one evaluation of
+ * c(F) X (Sec. 3.1): lower latency, lower throughput.  Larger launches give
+ * each lane-jump one warp.  0 never splits.  Results are identical either way.
+ * The threshold is per variant; variant -1 sets all three.  get returns the
+ * variant's threshold (VMT_EINVAL for a bad variant).
+ */
+int vmt_tune_jump_set(int variant, int64_t split_below);
+int64_t vmt_tune_jump_get(int variant);
 int vmt_autotune(int variant, int lanes, int64_t count, int64_t n_per_gen, int dtype, int reps, void* cuda_stream,
                  int* best_threads, double* best_ms);
 

@@ -54,6 +54,7 @@ def lib() -> ctypes.CDLL:
             "vmt_init_batch": (I, [PP, I, I, I64, P, P, P]),
             "vmt_jump": (I, [P, P, I64, P]),
             "vmt_jump_poly": (I, [I, U64, I, P, I64]),
+            "vmt_prepare": (I, [I, P]),
             "vmt_generate": (I, [P, I64, I, P, P]),
             "vmt_generate_multi": (I, [P, I, P, P, P, P]),
             "vmt_generate_host": (I, [P, I64, I, P, P]),
@@ -86,6 +87,8 @@ def lib() -> ctypes.CDLL:
             "vmt_server_destroy": (None, [P]),
             "vmt_tune_set": (I, [I, I, I]),
             "vmt_tune_get": (I, [I, I]),
+            "vmt_tune_jump_set": (I, [I, I64]),
+            "vmt_tune_jump_get": (I64, [I]),
             "vmt_autotune": (I, [I, I, I64, I64, I, I, P, P, P]),
         }
         for name, (res, args) in sigs.items():
@@ -260,7 +263,7 @@ SERVER_QUEUED, SERVER_RUNNING, SERVER_DONE = 0, 1, 2
 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("state_budget_bytes", ctypes.c_int64), ("output_budget_bytes", ctypes.c_int64),
-                ("max_batch", ctypes.c_int)]
+                ("max_batch", ctypes.c_int), ("reserve", ctypes.c_int)]
 
 
 class _Request(ctypes.Structure):
@@ -271,14 +274,16 @@ class _Request(ctypes.Structure):
 class _Counters(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("queued", "in_flight_batches", "batches", "completed", "failed",
                                              "bytes_out", "state_bytes_in_use", "output_bytes_in_use",
-                                             "peak_state_bytes", "peak_output_bytes")]
+                                             "peak_state_bytes", "peak_output_bytes")] + \
+        [(n, ctypes.c_double) for n in ("host_launch_s", "init_gpu_s", "batch_gpu_s")]
 
 
 class Server:
     """Continuous-batching request server (vmt_server_*)."""
 
-    def __init__(self, state_budget: int = 8 << 30, output_budget: int = 32 << 30, max_batch: int = 4096):
-        cfg = _ServerConfig(int(state_budget), int(output_budget), int(max_batch))
+    def __init__(self, state_budget: int = 8 << 30, output_budget: int = 32 << 30, max_batch: int = 4096,
+                 reserve: bool = False):
+        cfg = _ServerConfig(int(state_budget), int(output_budget), int(max_batch), int(bool(reserve)))
         h = ctypes.c_void_p()
         _check(lib().vmt_server_create(ctypes.byref(h), ctypes.byref(cfg)))
         self._h = h
@@ -336,6 +341,16 @@ def tune_set(variant: str, lanes: int, threads: int) -> None:
     _check(lib().vmt_tune_set(VARIANTS[variant], int(lanes), int(threads)))
 
 
+def tune_jump(variant: str, split_below: int | None = None) -> int:
+    """Jump launches of the variant with fewer lane-jumps than split_below use
+    one CTA per lane-jump; returns the value in force before the call (None:
+    just read)."""
+    old = int(lib().vmt_tune_jump_get(VARIANTS[variant]))
+    if split_below is not None:
+        _check(lib().vmt_tune_jump_set(VARIANTS[variant], int(split_below)))
+    return old
+
+
 def tune_get(variant: str, lanes: int) -> int:
     return _check(lib().vmt_tune_get(VARIANTS[variant], int(lanes)))
 
@@ -347,6 +362,11 @@ def autotune(variant: str, lanes: int, count: int, n_per_gen: int, dtype: str = 
     _check(lib().vmt_autotune(VARIANTS[variant], int(lanes), int(count), int(n_per_gen), DTYPES[dtype], int(reps),
                               _stream_handle(stream), ctypes.byref(t), ctypes.byref(ms)))
     return t.value, ms.value
+
+
+def prepare(variant: str, stream=None) -> None:
+    """Build the variant's polynomial tables now instead of on first use."""
+    _check(lib().vmt_prepare(VARIANTS[variant], _stream_handle(stream)))
 
 
 def jump_poly(variant: str, d: int, log2_extra: int = 0) -> np.ndarray:

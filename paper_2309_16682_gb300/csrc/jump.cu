@@ -24,6 +24,8 @@
 // form and then applies its period certification with the parity vector
 // (1, 0, 0, 0x13c9e684): when the parity of <p, w_0> is even the lowest set
 // bit of p is flipped in w_0.
+#include <atomic>
+
 #include "vmt_device.cuh"
 
 namespace vmt {
@@ -111,16 +113,65 @@ template <> __device__ __forceinline__ uint4 zero_unit<uint4>() { return make_ui
 // lane, RING units of sequence per warp, C coefficients per refill.
 struct JMT32 {
     using U = uint32_t;
-    static constexpr int N = 624, MM = 397, R = 20, RING = 2560, C = 640, G = N - MM;
+    static constexpr int N = 624, MM = 397, R = 20, RING = 2560, C = 640, G = N - MM, PRE = 0;
 };
 struct JMT64 {
     using U = unsigned long long;
-    static constexpr int N = 312, MM = 156, R = 10, RING = 1280, C = 320, G = N - MM;
+    static constexpr int N = 312, MM = 156, R = 10, RING = 1280, C = 320, G = N - MM, PRE = 0;
 };
+// SFMT: PRE units after the ring hold the chain-free parts of 32 new elements
 struct JSFMT {
     using U = uint4;
-    static constexpr int N = 156, MM = 122, R = 5, RING = 640, C = 160, G = 160;
+    static constexpr int N = 156, MM = 122, R = 5, RING = 600, C = 160, G = 160, PRE = 32;
 };
+
+// SFMT19937 recurrence split in two: the part of w_q from w_{q-N} and
+// w_{q-N+M}, which for 32 consecutive q only needs elements at least two
+// places back and so can be computed in parallel, and the serial rest from
+// w_{q-2} (128-bit right shift by 8) and w_{q-1} (32-bit left shifts by 18).
+__device__ __forceinline__ uint4 sfmt_pre(uint4 a, uint4 b)
+{
+    uint4 p;
+    p.x = a.x ^ (a.x << 8) ^ ((b.x >> 11) & kSfmtMask[0]);
+    p.y = a.y ^ __funnelshift_l(a.x, a.y, 8) ^ ((b.y >> 11) & kSfmtMask[1]);
+    p.z = a.z ^ __funnelshift_l(a.y, a.z, 8) ^ ((b.z >> 11) & kSfmtMask[2]);
+    p.w = a.w ^ __funnelshift_l(a.z, a.w, 8) ^ ((b.w >> 11) & kSfmtMask[3]);
+    return p;
+}
+__device__ __forceinline__ uint4 sfmt_chain(uint4 p, uint4 c, uint4 d)
+{
+    uint4 w;
+    w.x = p.x ^ __funnelshift_r(c.x, c.y, 8) ^ (d.x << 18);
+    w.y = p.y ^ __funnelshift_r(c.y, c.z, 8) ^ (d.y << 18);
+    w.z = p.z ^ __funnelshift_r(c.z, c.w, 8) ^ (d.z << 18);
+    w.w = p.w ^ (c.w >> 8) ^ (d.w << 18);
+    return w;
+}
+
+// One thread runs the chain through n <= 32 elements whose chain-free parts
+// are pre[0..n), writing them to ring[iq], ring[iq + 1], ... (modulo RG);
+// c and d are w_{q-2} and w_{q-1} and are carried on.  The parts are read
+// eight at a time ahead of the chain (the compiler cannot move a read of pre
+// above a write of the ring, which it must assume may alias).
+template <int RG>
+__device__ __forceinline__ void sfmt_chain_run(const uint4* pre, uint4* ring, int iq, int n, uint4& c, uint4& d)
+{
+    for (int u0 = 0; u0 < n; u0 += 8) {
+        uint4 p[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) p[k] = pre[u0 + k];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (u0 + k < n) {
+                const uint4 w = sfmt_chain(p[k], c, d);
+                ring[iq] = w;
+                iq = iq + 1 == RG ? 0 : iq + 1;
+                c = d;
+                d = w;
+            }
+        }
+    }
+}
 
 // extend the sequence: units [gen, gen + G) of the ring
 template <class J>
@@ -149,26 +200,20 @@ __device__ __forceinline__ void extend<JMT64>(unsigned long long* ring, int gen,
 template <>
 __device__ __forceinline__ void extend<JSFMT>(uint4* ring, int gen, int lane)
 {
-    // four lanes, one 32-bit sub-word each; serial over the G new elements
+    // 32 elements at a time: every lane the chain-free part of one element,
+    // then lane 0 the chain through all 32
     constexpr int RG = JSFMT::RING, NN = JSFMT::N, MMM = JSFMT::MM;
-    if (lane >= 4) return;
-    const int j = lane;
-    const uint32_t K = kSfmtMask[j];
-    uint32_t* r32 = reinterpret_cast<uint32_t*>(ring);
-    uint32_t d = r32[4 * ((gen - 1) % RG) + j];   // w_{q-1}
-    uint32_t c = r32[4 * ((gen - 2) % RG) + j];   // w_{q-2}
-    for (int u = 0; u < JSFMT::G; ++u) {
-        const int q = gen + u;
-        const uint32_t wa = r32[4 * ((q - NN) % RG) + j];
-        const uint32_t wb = r32[4 * ((q - NN + MMM) % RG) + j];
-        uint32_t am1 = __shfl_up_sync(0xFu, wa, 1, 4);
-        uint32_t cp1 = __shfl_down_sync(0xFu, c, 1, 4);
-        if (j == 0) am1 = 0u;
-        if (j == 3) cp1 = 0u;
-        const uint32_t nw = wa ^ __funnelshift_l(am1, wa, 8) ^ ((wb >> 11) & K) ^ __funnelshift_r(c, cp1, 8) ^ (d << 18);
-        r32[4 * (q % RG) + j] = nw;
-        c = d;
-        d = nw;
+    static_assert(JSFMT::G % 32 == 0 && NN - MMM >= 32, "blocks of 32 elements");
+    uint4* pre = ring + RG;
+    for (int s0 = gen; s0 < gen + JSFMT::G; s0 += 32) {
+        const int q = s0 + lane;
+        pre[lane] = sfmt_pre(ring[(q - NN) % RG], ring[(q - NN + MMM) % RG]);
+        __syncwarp();
+        if (lane == 0) {
+            uint4 c = ring[(s0 - 2) % RG], d = ring[(s0 - 1) % RG];
+            sfmt_chain_run<RG>(pre, ring, s0 % RG, 32, c, d);
+        }
+        __syncwarp();
     }
 }
 
@@ -281,7 +326,7 @@ __global__ void __launch_bounds__(kJumpWarps * 32) jump_kernel(const JumpItem* i
     constexpr int N = J::N, R = J::R, RING = J::RING, C = J::C;
     static_assert(RING % R == 0 && C % R == 0, "groups must not wrap the ring");
     static_assert(RING >= C + 32 * R + J::G && RING >= N + J::G, "ring too small");
-    __shared__ __align__(16) U ring_all[kJumpWarps][RING];
+    __shared__ __align__(16) U ring_all[kJumpWarps][RING + J::PRE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long item = static_cast<long long>(blockIdx.x) * kJumpWarps + warp;
     if (item >= nitems) return;  // whole warp leaves together
@@ -326,11 +371,196 @@ __global__ void __launch_bounds__(kJumpWarps * 32) jump_kernel(const JumpItem* i
         if (j0 + r < N) dst[static_cast<long long>(j0 + r) * it.dst_stride] = acc[r];
 }
 
-template <class J>
+// ---------------------------------------------------------------------------
+// jump kernel for small launches: one CTA per lane-jump
+// ---------------------------------------------------------------------------
+// The same evaluation with one lane-jump spread over the W warps of a CTA by
+// splitting the coefficients of c: the CTA extends the sequence into a large
+// shared ring (the whole extended sequence for MT19937-32/64, two rounds for
+// SFMT19937), warp w walks the w-th slice of the round's coefficients exactly
+// as one warp of jump_kernel walks all of them (lane L holding output units
+// [L R, L R + R)), and at the end the W partial results are XORed.  A
+// lane-jump costs about as many instructions as in jump_kernel, but its
+// latency is W times shorter, which is what launches of a few hundred items
+// (a batch of requests, the lanes of a few generators) are bound by.
+struct CMT32 {
+    using U = uint32_t;
+    static constexpr int N = 624, MM = 397, G = N - MM, R = 20, W = 16, L = 21120, PRE = 0;
+};
+struct CMT64 {
+    using U = unsigned long long;
+    static constexpr int N = 312, MM = 156, G = N - MM, R = 10, W = 16, L = 20760, PRE = 0;
+};
+struct CSFMT {
+    using U = uint4;
+    static constexpr int N = 156, MM = 122, G = 0, R = 5, W = 16, L = 12000, PRE = 32;
+};
+// coefficients per round: the ring holds the round's window of C + 33 R units
+// plus one extension step
+template <class S> __host__ __device__ constexpr int cta_round() { return (S::L - 33 * S::R - S::G) / (S::R * S::W) * (S::R * S::W); }
+template <class S> __host__ __device__ constexpr size_t cta_smem()
+{
+    return static_cast<size_t>(S::L + S::PRE) * sizeof(typename S::U);
+}
+
+__device__ __forceinline__ int wrap_sub(int p, int L) { return p >= L ? p - L : p; }
+
+// extend the ring from unit gen up to (at least) unit need; every thread
+// calls it with the same arguments and gets the same new gen
+template <class S>
+__device__ __forceinline__ int cta_extend(typename S::U* ring, int gen, int need, int tid);
+
+template <class S, class T>
+__device__ __forceinline__ int cta_extend_mt(typename S::U* ring, int gen, int need, int tid)
+{
+    constexpr int L = S::L;
+    while (gen < need) {
+        if (tid < S::G) {
+            const int q = gen + tid;   // ring positions are taken modulo L
+            const int k = (q - S::N) % L;
+            ring[q % L] = T::twist(ring[k], ring[wrap_sub(k + 1, L)], ring[wrap_sub(k + S::MM, L)]);
+        }
+        gen += S::G;
+        __syncthreads();
+    }
+    return gen;
+}
+template <>
+__device__ __forceinline__ int cta_extend<CMT32>(uint32_t* ring, int gen, int need, int tid)
+{
+    return cta_extend_mt<CMT32, MT32>(ring, gen, need, tid);
+}
+template <>
+__device__ __forceinline__ int cta_extend<CMT64>(unsigned long long* ring, int gen, int need, int tid)
+{
+    return cta_extend_mt<CMT64, MT64>(ring, gen, need, tid);
+}
+// SFMT: 32 elements at a time, warp 1 computing their chain-free parts into
+// the 32 units after the ring and thread 0 running the chain through them;
+// the two warps meet at named barrier 1, the other warps wait at the end
+template <>
+__device__ __forceinline__ int cta_extend<CSFMT>(uint4* ring, int gen, int need, int tid)
+{
+    constexpr int L = CSFMT::L, NN = CSFMT::N, MMM = CSFMT::MM;
+    static_assert(NN - MMM >= 32 && CSFMT::W >= 2, "blocks of 32 elements, two warps");
+    uint4* pre = ring + L;
+    if (tid < 64) {
+        uint4 c = make_uint4(0u, 0u, 0u, 0u), d = c;
+        if (tid == 0 && gen < need) {
+            c = ring[(gen - 2) % L];
+            d = ring[(gen - 1) % L];
+        }
+        for (int s0 = gen; s0 < need; s0 += 32) {
+            const int cnt = min(32, need - s0);
+            const int lane = tid - 32;
+            if (lane >= 0 && lane < cnt) {
+                const int q = s0 + lane;
+                pre[lane] = sfmt_pre(ring[(q - NN) % L], ring[(q - NN + MMM) % L]);
+            }
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+            if (tid == 0) {
+                if (cnt == 32) sfmt_chain_run<L>(pre, ring, s0 % L, 32, c, d);   // full blocks: no predication
+                else sfmt_chain_run<L>(pre, ring, s0 % L, cnt, c, d);
+            }
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+        }
+    }
+    __syncthreads();
+    return need > gen ? need : gen;
+}
+
+template <class S>
+__global__ void __launch_bounds__(S::W * 32) jump_cta_kernel(const JumpItem* items, JumpGrid grid, const uint32_t* polys)
+{
+    using U = typename S::U;
+    constexpr int N = S::N, R = S::R, W = S::W, L = S::L, C = cta_round<S>();
+    static_assert(L % R == 0 && R * sizeof(U) % 16 == 0, "R-unit groups are aligned 16-byte loads that never wrap");
+    static_assert(C > 0 && L >= C + 33 * R + S::G && L >= N + S::G, "ring too small");
+    static_assert(W * 32 * R <= L && 32 * R >= N, "partial results must fit the ring");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    U* ring = reinterpret_cast<U*>(smem_raw);
+    const long long item = blockIdx.x;
+    JumpItem it;
+    if (items) it = items[item];
+    else if (!grid_item(grid, item, it)) return;   // the same answer for every thread
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int u = tid; u < N; u += W * 32) ring[u] = ld_unit<U>(it.src, static_cast<long long>(u) * it.src_stride);
+    __syncthreads();
+
+    const uint32_t* c = polys + static_cast<long long>(it.poly) * kPolyWords;
+    const int deg = it.deg;
+    const int j0 = lane * R;
+    U acc[R], wA[R], wB[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = zero_unit<U>();
+    int gen = N;
+    for (int i0 = 0; i0 <= deg; i0 += C) {
+        const int iend = min(i0 + C, deg + 1);
+        gen = cta_extend<S>(ring, gen, iend + 33 * R, tid);
+        // this warp's slice of the round's coefficients, a multiple of R long
+        const int span = ((iend - i0 + W * R - 1) / (W * R)) * R;
+        const int lo = i0 + warp * span, hi = min(lo + span, iend);
+        if (lo < hi) {
+            load_group<S>(ring, (lo + j0) % L, wA);
+            for (int ib = lo; ib < hi; ib += R) {
+                load_group<S>(ring, (ib + R + j0) % L, wB);
+                const int wi = ib >> 5, sh = ib & 31;
+                const unsigned long long two = static_cast<unsigned long long>(__ldg(c + wi)) |
+                                               (static_cast<unsigned long long>(__ldg(c + wi + 1)) << 32);
+                const uint32_t bits = static_cast<uint32_t>(two >> sh) & ((1u << R) - 1u);
+                if (bits) ApplyAll<S, 0>::run(bits, acc, wA, wB);
+#pragma unroll
+                for (int r = 0; r < R; ++r) wA[r] = wB[r];
+            }
+        }
+        __syncthreads();   // the round is consumed before the ring moves on
+    }
+    // XOR of the W partial results
+#pragma unroll
+    for (int r = 0; r < R; ++r) ring[warp * 32 * R + j0 + r] = acc[r];
+    __syncthreads();
+    U* dst = reinterpret_cast<U*>(it.dst);
+    for (int j = tid; j < N; j += W * 32) {
+        U x = ring[j];
+#pragma unroll
+        for (int w = 1; w < W; ++w) x = x ^ ring[w * 32 * R + j];
+        dst[static_cast<long long>(j) * it.dst_stride] = x;
+    }
+}
+
+// Launches of fewer items than this use the CTA-per-item kernel, per variant
+// (the crossover in lane-jumps per second measured on GB300: about 4096 for
+// MT19937-32/64, about 512 for SFMT19937, whose serial chain makes the CTA
+// kernel's lane-jump long).
+static std::atomic<long long> g_split_below[3] = {{4096}, {4096}, {512}};
+
+// the CTA kernels' dynamic shared memory limit, raised once per device
+template <class S>
+static cudaError_t cta_smem_attr()
+{
+    constexpr int kMaxDev = 64;
+    static std::atomic<bool> done[kMaxDev];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDev && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    e = cudaFuncSetAttribute(jump_cta_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(cta_smem<S>()));
+    if (e == cudaSuccess && dev >= 0 && dev < kMaxDev) done[dev].store(true, std::memory_order_release);
+    return e;
+}
+
+template <class J, class S>
 static cudaError_t launch_jump_t(const JumpItem* items, const JumpGrid& gr, long long nitems, const uint32_t* polys,
-                                 cudaStream_t st)
+                                 cudaStream_t st, long long split_below)
 {
     if (nitems <= 0) return cudaSuccess;
+    if (nitems < split_below) {
+        const cudaError_t e = cta_smem_attr<S>();
+        if (e != cudaSuccess) return e;
+        jump_cta_kernel<S><<<static_cast<unsigned>(nitems), S::W * 32, cta_smem<S>(), st>>>(items, gr, polys);
+        return cudaGetLastError();
+    }
     const long long grid = (nitems + kJumpWarps - 1) / kJumpWarps;
     jump_kernel<J><<<static_cast<unsigned>(grid), kJumpWarps * 32, 0, st>>>(items, gr, nitems, polys);
     return cudaGetLastError();
@@ -390,19 +620,26 @@ cudaError_t launch_seed(int variant, long long count, const unsigned long long* 
 cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s)
 {
     using namespace dev;
+    if (variant < 0 || variant > 2) return cudaErrorInvalidValue;
     const JumpGrid none{};
-    if (variant == VMT_MT19937_32) return launch_jump_t<JMT32>(items, none, nitems, polys, s);
-    if (variant == VMT_MT19937_64) return launch_jump_t<JMT64>(items, none, nitems, polys, s);
-    return launch_jump_t<JSFMT>(items, none, nitems, polys, s);
+    const long long sb = g_split_below[variant].load(std::memory_order_relaxed);
+    if (variant == VMT_MT19937_32) return launch_jump_t<JMT32, CMT32>(items, none, nitems, polys, s, sb);
+    if (variant == VMT_MT19937_64) return launch_jump_t<JMT64, CMT64>(items, none, nitems, polys, s, sb);
+    return launch_jump_t<JSFMT, CSFMT>(items, none, nitems, polys, s, sb);
 }
 
 cudaError_t launch_jump_grid(int variant, const JumpGrid& gr, long long nitems, const uint32_t* polys, cudaStream_t s)
 {
     using namespace dev;
-    if (variant == VMT_MT19937_32) return launch_jump_t<JMT32>(nullptr, gr, nitems, polys, s);
-    if (variant == VMT_MT19937_64) return launch_jump_t<JMT64>(nullptr, gr, nitems, polys, s);
-    return launch_jump_t<JSFMT>(nullptr, gr, nitems, polys, s);
+    if (variant < 0 || variant > 2) return cudaErrorInvalidValue;
+    const long long sb = g_split_below[variant].load(std::memory_order_relaxed);
+    if (variant == VMT_MT19937_32) return launch_jump_t<JMT32, CMT32>(nullptr, gr, nitems, polys, s, sb);
+    if (variant == VMT_MT19937_64) return launch_jump_t<JMT64, CMT64>(nullptr, gr, nitems, polys, s, sb);
+    return launch_jump_t<JSFMT, CSFMT>(nullptr, gr, nitems, polys, s, sb);
 }
+
+void set_jump_split_below(int variant, long long items) { dev::g_split_below[variant].store(items < 0 ? 0 : items); }
+long long get_jump_split_below(int variant) { return dev::g_split_below[variant].load(); }
 
 cudaError_t launch_fill_int(int* p, long long n, int value, cudaStream_t s)
 {

@@ -70,12 +70,12 @@ struct Req {
     int64_t state_bytes = 0;
     int64_t chunks = 1;      // generators it runs on (one per chunk)
     bool admitted = false;   // its output bytes count against the budget
-    cudaStream_t free_stream = nullptr;   // the stream its output was produced on
     double t_submit = 0, t_done = 0;
 };
 
 struct Slot {
-    cudaStream_t s_init = nullptr, s_gen = nullptr;   // this slot's batches run here
+    cudaStream_t s_init[3] = {}, s_gen = nullptr;   // this slot's batches run here (init: one per variant)
+    cudaEvent_t ev_init[3] = {};                    // end of a variant's initialisation
     vmt::UnitDesc* h_units = nullptr;
     vmt::UnitDesc* d_units = nullptr;
     int* d_counter = nullptr;
@@ -83,6 +83,7 @@ struct Slot {
     uint64_t* h_jumps = nullptr;
     int2* h_map = nullptr;    // (request, chunk) of every chunk state
     int2* d_map = nullptr;
+    cudaEvent_t ev[3] = {};   // batch start, end of initialisation, end of generation
     bool busy = false;
 };
 
@@ -97,6 +98,7 @@ struct Batch {
     std::vector<uint64_t> ids;
     std::vector<vmt_state*> states;
     int64_t state_bytes = 0;
+    int rc = VMT_OK;                     // launch error, given to its requests at retirement
     std::atomic<bool> gpu_done{false};   // set by the stream's host function
     double t_done = 0;
     HostDone cb;
@@ -114,6 +116,11 @@ struct vmt_server {
     Slot slots[kSlots];
     int64_t used_state = 0, used_out = 0, peak_state = 0, peak_out = 0;
     int64_t batches = 0, completed = 0, failed = 0, bytes_out = 0;
+    double host_launch_s = 0, init_gpu_s = 0, batch_gpu_s = 0;
+    cudaMemPool_t pool = nullptr;   // states and outputs
+    // Memory is freed on a stream of its own, only ever after the kernels that
+    // used it have finished, so reuse of a freed block never waits for other work.
+    cudaStream_t s_free = nullptr;
     uint64_t next_id = 1;
     bool stop = false;
     int device = 0;
@@ -134,111 +141,144 @@ void CUDART_CB on_batch_done(void* p)
     srv->cv_work.notify_all();
 }
 
-// Launch one batch.  Per kernel group: batched initialisation of the
-// requests' generators on the slot's init stream; requests longer than one
+// Launch one batch.  Per variant, on that variant's init stream of the slot
+// (the three variants initialise concurrently): one batched initialisation
+// of all its requests' generators (seeding and jump offsets once, the lane
+// fan-out per kernel group (lanes, output type)); requests longer than one
 // chunk (vmt::chunk_words) are cut at chunk boundaries, chunk c >= 1 getting
 // its own generator, the request's lanes advanced to S word c * chunk (one
-// device-side jump per lane); then one persistent ragged launch over all
-// chunks, longest first, on the slot's generation stream.
+// device-side jump per lane).  Then per kernel group one persistent ragged
+// launch over all chunks, longest first, on the slot's generation stream,
+// after its variant's initialisation.
 int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
 {
     Slot& sl = s->slots[b->slot];
-    cudaStream_t s_init = sl.s_init, s_gen = sl.s_gen;
-    std::map<std::tuple<int, int, int>, std::vector<size_t>> groups;
-    for (size_t i = 0; i < rq.size(); ++i) groups[{rq[i]->r.variant, rq[i]->r.lanes, rq[i]->r.dtype}].push_back(i);
+    cudaStream_t s_gen = sl.s_gen;
+    cudaEventRecord(sl.ev[0], s_gen);
+    // variant -> kernel group (lanes, dtype) -> request indices
+    std::map<int, std::map<std::pair<int, int>, std::vector<size_t>>> by_variant;
+    for (size_t i = 0; i < rq.size(); ++i)
+        by_variant[rq[i]->r.variant][{rq[i]->r.lanes, rq[i]->r.dtype}].push_back(i);
     int64_t seed0 = 0, unit0 = 0, map0 = 0;
     int gk = 0;
     int rc = VMT_OK;
-    for (auto& kv : groups) {
-        const int variant = std::get<0>(kv.first), lanes = std::get<1>(kv.first), dtype = std::get<2>(kv.first);
-        const auto& idx = kv.second;
-        const int64_t k = static_cast<int64_t>(idx.size());
-        const int wpo = words_per_out(variant, dtype);
-        const int64_t C = vmt::chunk_words(variant, lanes);
-        for (int64_t i = 0; i < k; ++i) {
-            sl.h_seeds[seed0 + i] = rq[idx[static_cast<size_t>(i)]]->r.seed;
-            sl.h_jumps[seed0 + i] = rq[idx[static_cast<size_t>(i)]]->r.jump;
-        }
-        vmt_state* st = nullptr;
-        rc = vmt::init_batch_impl(&st, variant, lanes, k, sl.h_seeds + seed0, sl.h_jumps + seed0, s_init, true);
-        if (rc) return rc;
-        b->states.push_back(st);
-        for (int64_t i = 0; i < k; ++i) {
-            Req* q = rq[idx[static_cast<size_t>(i)]];
-            if (cudaMallocAsync(&q->out, static_cast<size_t>(std::max<int64_t>(q->bytes, 16)), s_init) != cudaSuccess)
-                return VMT_ENOMEM;
-            q->free_stream = s_gen;
-        }
-        // chunks: request i, chunk c in 1..P_i-1 (at most kChunkRows + 1 chunks)
-        int64_t nchunk = 0;
-        for (int64_t i = 0; i < k; ++i) {
-            const int64_t w = rq[idx[static_cast<size_t>(i)]]->r.n * wpo;
-            const int64_t P = n_chunks(variant, lanes, w);
-            for (int64_t c = 1; c < P; ++c) sl.h_map[map0 + nchunk++] = make_int2(static_cast<int>(i), static_cast<int>(c));
-        }
-        vmt_state* cst = nullptr;
-        if (nchunk) {
-            rc = vmt::alloc_states_async(&cst, variant, lanes, nchunk, s_init);
-            if (rc) return rc;
-            b->states.push_back(cst);
-            cudaMemcpyAsync(sl.d_map + map0, sl.h_map + map0, static_cast<size_t>(nchunk) * sizeof(int2),
-                            cudaMemcpyHostToDevice, s_init);
-            rc = vmt::launch_chunk_jumps(st, cst, sl.d_map + map0, s_init);
-            if (rc) return rc;
-        }
-        cudaEvent_t ev;
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        cudaEventRecord(ev, s_init);
-        cudaStreamWaitEvent(s_gen, ev, 0);
-        cudaEventDestroy(ev);
-        // units: chunk 0 of every request on its own generator, chunks >= 1 on
-        // the chunk generators; the last chunk takes the rest of the request
-        const int64_t gen_bytes = vmt::state_bytes_per_gen(variant, lanes);
-        const int eb = out_bytes(dtype);
-        std::vector<vmt::UnitDesc> units;
-        int64_t ck = 0;
-        for (int64_t i = 0; i < k; ++i) {
-            Req* q = rq[idx[static_cast<size_t>(i)]];
-            const int64_t w = q->r.n * wpo;
-            if (w == 0) continue;
-            const int64_t P = n_chunks(variant, lanes, w);
-            for (int64_t c = 0; c < P; ++c) {
-                vmt::UnitDesc u{};
-                const int64_t w0 = c * C, w1 = (c == P - 1) ? w : (c + 1) * C;
-                if (c == 0) {
-                    u.state = static_cast<char*>(st->d_states) + i * gen_bytes;
-                    u.pos = st->d_pos + i;
-                } else {
-                    u.state = static_cast<char*>(cst->d_states) + ck * gen_bytes;
-                    u.pos = cst->d_pos + ck;
-                    ++ck;
-                }
-                u.total = w1 - w0;
-                u.out = static_cast<char*>(q->out) + (w0 / wpo) * eb;
-                units.push_back(u);
+    for (auto& vv : by_variant) {
+        const int variant = vv.first;
+        cudaStream_t s_init = sl.s_init[variant];
+        cudaStreamWaitEvent(s_init, sl.ev[0], 0);
+        // one initialisation for the variant, one state object per group
+        std::vector<int> lanes_of;
+        std::vector<int64_t> counts;
+        int64_t k_all = 0;
+        for (auto& kv : vv.second) {
+            lanes_of.push_back(kv.first.first);
+            counts.push_back(static_cast<int64_t>(kv.second.size()));
+            for (size_t i : kv.second) {
+                sl.h_seeds[seed0 + k_all] = rq[i]->r.seed;
+                sl.h_jumps[seed0 + k_all] = rq[i]->r.jump;
+                ++k_all;
             }
         }
-        std::stable_sort(units.begin(), units.end(),
-                         [](const vmt::UnitDesc& x, const vmt::UnitDesc& y) { return x.total > y.total; });
-        const int64_t nu = static_cast<int64_t>(units.size());
-        if (nu) {
-            std::memcpy(sl.h_units + unit0, units.data(), static_cast<size_t>(nu) * sizeof(vmt::UnitDesc));
-            cudaMemcpyAsync(sl.d_units + unit0, sl.h_units + unit0, static_cast<size_t>(nu) * sizeof(vmt::UnitDesc),
-                            cudaMemcpyHostToDevice, s_gen);
-            rc = vmt::launch_unit_table(variant, lanes, dtype, sl.d_units + unit0, nu, sl.d_counter + gk, s_gen);
-            if (rc) return rc;
+        const int nsub = static_cast<int>(counts.size());
+        std::vector<vmt_state*> sts(static_cast<size_t>(nsub), nullptr);
+        rc = vmt::init_multi_impl(sts.data(), variant, nsub, lanes_of.data(), counts.data(), sl.h_seeds + seed0,
+                                  sl.h_jumps + seed0, s_init, true, s->pool);
+        if (rc) return rc;
+        for (vmt_state* st : sts) b->states.push_back(st);
+        seed0 += k_all;
+        // per group: outputs, chunk generators and their jumps
+        std::vector<vmt_state*> csts(static_cast<size_t>(nsub), nullptr);
+        int gi = 0;
+        for (auto& kv : vv.second) {
+            const int lanes = kv.first.first, dtype = kv.first.second;
+            const auto& idx = kv.second;
+            const int64_t k = static_cast<int64_t>(idx.size());
+            const int wpo = words_per_out(variant, dtype);
+            for (int64_t i = 0; i < k; ++i) {
+                Req* q = rq[idx[static_cast<size_t>(i)]];
+                if (cudaMallocFromPoolAsync(&q->out, static_cast<size_t>(std::max<int64_t>(q->bytes, 16)), s->pool,
+                                            s_init) != cudaSuccess)
+                    return VMT_ENOMEM;
+            }
+            // chunks: request i, chunk c in 1..P_i-1
+            int64_t nchunk = 0;
+            for (int64_t i = 0; i < k; ++i) {
+                const int64_t P = n_chunks(variant, lanes, rq[idx[static_cast<size_t>(i)]]->r.n * wpo);
+                for (int64_t c = 1; c < P; ++c)
+                    sl.h_map[map0 + nchunk++] = make_int2(static_cast<int>(i), static_cast<int>(c));
+            }
+            if (nchunk) {
+                rc = vmt::alloc_states_async(&csts[static_cast<size_t>(gi)], variant, lanes, nchunk, s_init, s->pool);
+                if (rc) return rc;
+                b->states.push_back(csts[static_cast<size_t>(gi)]);
+                cudaMemcpyAsync(sl.d_map + map0, sl.h_map + map0, static_cast<size_t>(nchunk) * sizeof(int2),
+                                cudaMemcpyHostToDevice, s_init);
+                rc = vmt::launch_chunk_jumps(sts[static_cast<size_t>(gi)], csts[static_cast<size_t>(gi)],
+                                             sl.d_map + map0, s_init);
+                if (rc) return rc;
+            }
+            map0 += nchunk;
+            ++gi;
         }
-        seed0 += k;
-        unit0 += nu;
-        map0 += nchunk;
-        ++gk;
+        cudaEventRecord(sl.ev_init[variant], s_init);
+        cudaStreamWaitEvent(s_gen, sl.ev_init[variant], 0);
+        // generation per group: chunk 0 of every request on its own generator,
+        // chunks >= 1 on the chunk generators; the last chunk takes the rest
+        gi = 0;
+        for (auto& kv : vv.second) {
+            const int lanes = kv.first.first, dtype = kv.first.second;
+            const auto& idx = kv.second;
+            const int64_t k = static_cast<int64_t>(idx.size());
+            const int wpo = words_per_out(variant, dtype);
+            const int64_t C = vmt::chunk_words(variant, lanes);
+            const int64_t gen_bytes = vmt::state_bytes_per_gen(variant, lanes);
+            const int eb = out_bytes(dtype);
+            const vmt_state* st = sts[static_cast<size_t>(gi)];
+            const vmt_state* cst = csts[static_cast<size_t>(gi)];
+            std::vector<vmt::UnitDesc> units;
+            int64_t ck = 0;
+            for (int64_t i = 0; i < k; ++i) {
+                Req* q = rq[idx[static_cast<size_t>(i)]];
+                const int64_t w = q->r.n * wpo;
+                if (w == 0) continue;
+                const int64_t P = n_chunks(variant, lanes, w);
+                for (int64_t c = 0; c < P; ++c) {
+                    vmt::UnitDesc u{};
+                    const int64_t w0 = c * C, w1 = (c == P - 1) ? w : (c + 1) * C;
+                    if (c == 0) {
+                        u.state = static_cast<char*>(st->d_states) + i * gen_bytes;
+                        u.pos = st->d_pos + i;
+                    } else {
+                        u.state = static_cast<char*>(cst->d_states) + ck * gen_bytes;
+                        u.pos = cst->d_pos + ck;
+                        ++ck;
+                    }
+                    u.total = w1 - w0;
+                    u.out = static_cast<char*>(q->out) + (w0 / wpo) * eb;
+                    units.push_back(u);
+                }
+            }
+            std::stable_sort(units.begin(), units.end(),
+                             [](const vmt::UnitDesc& x, const vmt::UnitDesc& y) { return x.total > y.total; });
+            const int64_t nu = static_cast<int64_t>(units.size());
+            if (nu) {
+                std::memcpy(sl.h_units + unit0, units.data(), static_cast<size_t>(nu) * sizeof(vmt::UnitDesc));
+                cudaMemcpyAsync(sl.d_units + unit0, sl.h_units + unit0,
+                                static_cast<size_t>(nu) * sizeof(vmt::UnitDesc), cudaMemcpyHostToDevice, s_gen);
+                rc = vmt::launch_unit_table(variant, lanes, dtype, sl.d_units + unit0, nu, sl.d_counter + gk, s_gen);
+                if (rc) return rc;
+            }
+            unit0 += nu;
+            ++gk;
+            ++gi;
+        }
     }
     return VMT_OK;
 }
 
 // Finished batches leave the in-flight list; returns their states, to be
 // released after the lock is dropped (no CUDA call is made under the lock).
-std::vector<std::pair<vmt_state*, cudaStream_t>> retire(vmt_server* s)   // with s->mu held
+std::vector<std::pair<vmt_state*, cudaStream_t>> retire(vmt_server* s, std::vector<int>& slots)   // with s->mu held
 {
     std::vector<std::pair<vmt_state*, cudaStream_t>> to_free;
     for (size_t i = 0; i < s->inflight.size();) {
@@ -248,19 +288,22 @@ std::vector<std::pair<vmt_state*, cudaStream_t>> retire(vmt_server* s)   // with
             continue;
         }
         s->inflight.erase(s->inflight.begin() + static_cast<std::ptrdiff_t>(i));
-        for (vmt_state* st : b->states) to_free.push_back({st, s->slots[b->slot].s_gen});
+        for (vmt_state* st : b->states) to_free.push_back({st, s->s_free});
         s->used_state -= b->state_bytes;
         for (uint64_t id : b->ids) {
             auto it = s->reqs.find(id);
             if (it == s->reqs.end()) continue;
-            if (it->second.status == VMT_SERVER_RUNNING) {
+            if (it->second.status == VMT_SERVER_RUNNING && b->rc) {
+                it->second.status = b->rc;   // reported only now: its batch's kernels have finished
+                ++s->failed;
+            } else if (it->second.status == VMT_SERVER_RUNNING) {
                 it->second.status = VMT_SERVER_DONE;
                 it->second.t_done = b->t_done;
                 ++s->completed;
                 s->bytes_out += it->second.bytes;
             }
         }
-        s->slots[b->slot].busy = false;
+        slots.push_back(b->slot);   // its events are read before the slot is reused
         delete b;
         s->cv_done.notify_all();
     }
@@ -272,11 +315,21 @@ void worker_main(vmt_server* s)
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
-        const auto to_free = retire(s);
-        if (!to_free.empty()) {
+        std::vector<int> done_slots;
+        const auto to_free = retire(s, done_slots);
+        if (!done_slots.empty()) {
             lk.unlock();
             for (const auto& f : to_free) vmt::free_state_async(f.first, f.second);
+            float t_init = 0, t_all = 0, ms = 0;
+            for (int i : done_slots) {
+                if (cudaEventElapsedTime(&ms, s->slots[i].ev[0], s->slots[i].ev[1]) == cudaSuccess) t_init += ms;
+                if (cudaEventElapsedTime(&ms, s->slots[i].ev[0], s->slots[i].ev[2]) == cudaSuccess) t_all += ms;
+            }
+            cudaGetLastError();
             lk.lock();
+            s->init_gpu_s += 1e-3 * t_init;
+            s->batch_gpu_s += 1e-3 * t_all;
+            for (int i : done_slots) s->slots[i].busy = false;
         }
         if (s->stop && s->queue.empty() && s->inflight.empty()) break;
         int slot = -1;
@@ -333,16 +386,19 @@ void worker_main(vmt_server* s)
         s->slots[slot].busy = true;
         ++s->batches;
         lk.unlock();
+        const double t0 = now_s();
         const int rc = launch_batch(s, b, rq);
+        // end of initialisation: all variants' init streams joined into the first
+        Slot& sl = s->slots[slot];
+        cudaStreamWaitEvent(sl.s_init[0], sl.ev_init[1], 0);
+        cudaStreamWaitEvent(sl.s_init[0], sl.ev_init[2], 0);
+        cudaEventRecord(sl.ev[1], sl.s_init[0]);
+        cudaEventRecord(s->slots[slot].ev[2], s->slots[slot].s_gen);
         cudaLaunchHostFunc(s->slots[slot].s_gen, on_batch_done, &b->cb);
+        const double t1 = now_s();
         lk.lock();
-        if (rc) {
-            for (uint64_t id : ids) {
-                Req& q = s->reqs[id];
-                q.status = rc;
-                ++s->failed;
-            }
-        }
+        s->host_launch_s += t1 - t0;
+        b->rc = rc;
         s->inflight.push_back(b);
     }
 }
@@ -364,13 +420,26 @@ int vmt_server_create(vmt_server** out, const vmt_server_config* cfg)
     vmt_server* s = new vmt_server();
     s->cfg = *cfg;
     cudaGetDevice(&s->device);
-    bool ok = true;
+    // the server's pool keeps up to both budgets' bytes mapped between requests
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = s->device;
+    bool ok = cudaMemPoolCreate(&s->pool, &props) == cudaSuccess;
+    if (ok) {
+        uint64_t keep = static_cast<uint64_t>(cfg->state_budget_bytes) + static_cast<uint64_t>(cfg->output_budget_bytes);
+        ok = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&s->s_free, cudaStreamNonBlocking) == cudaSuccess;
+    }
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     for (int i = 0; i < kSlots && ok; ++i) {
         Slot& sl = s->slots[i];
         const size_t n = static_cast<size_t>(cfg->max_batch);
         const size_t nu = static_cast<size_t>(kMaxUnits);
-        ok = cudaStreamCreateWithFlags(&sl.s_init, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&sl.s_gen, cudaStreamNonBlocking) == cudaSuccess &&
+        // initialisation (short jump launches) is scheduled ahead of generation
+        // blocks still waiting for an SM
+        ok = cudaStreamCreateWithFlags(&sl.s_gen, cudaStreamNonBlocking) == cudaSuccess &&
              cudaHostAlloc(reinterpret_cast<void**>(&sl.h_units), nu * sizeof(vmt::UnitDesc), 0) == cudaSuccess &&
              cudaMalloc(reinterpret_cast<void**>(&sl.d_units), nu * sizeof(vmt::UnitDesc)) == cudaSuccess &&
              cudaHostAlloc(reinterpret_cast<void**>(&sl.h_map), nu * sizeof(int2), 0) == cudaSuccess &&
@@ -378,6 +447,30 @@ int vmt_server_create(vmt_server** out, const vmt_server_config* cfg)
              cudaMalloc(reinterpret_cast<void**>(&sl.d_counter), kMaxGroups * sizeof(int)) == cudaSuccess &&
              cudaHostAlloc(reinterpret_cast<void**>(&sl.h_seeds), n * 8, 0) == cudaSuccess &&
              cudaHostAlloc(reinterpret_cast<void**>(&sl.h_jumps), n * 8, 0) == cudaSuccess;
+        for (int e = 0; e < 3 && ok; ++e)
+            ok = cudaEventCreate(&sl.ev[e]) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&sl.ev_init[e], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaStreamCreateWithPriority(&sl.s_init[e], cudaStreamNonBlocking, prio_hi) == cudaSuccess;
+    }
+    if (ok && cfg->reserve) {
+        // map the budgets now: one allocation of their sum, freed back to the pool
+        void* p = nullptr;
+        const size_t bytes = static_cast<size_t>(cfg->state_budget_bytes) + static_cast<size_t>(cfg->output_budget_bytes);
+        if (cudaMallocFromPoolAsync(&p, bytes, s->pool, s->slots[0].s_gen) != cudaSuccess) {
+            cudaGetLastError();
+            vmt::set_last_error("vmt_server_create: the budgets do not fit in device memory");
+            vmt_server_destroy(s);
+            return VMT_ENOMEM;
+        }
+        ok = cudaFreeAsync(p, s->slots[0].s_gen) == cudaSuccess &&
+             cudaStreamSynchronize(s->slots[0].s_gen) == cudaSuccess;
+        for (int v = VMT_MT19937_32; v <= VMT_SFMT19937 && ok; ++v) {
+            const int rc = vmt_prepare(v, s->slots[0].s_gen);
+            if (rc) {
+                vmt_server_destroy(s);
+                return rc;
+            }
+        }
     }
     if (!ok) {
         vmt::set_last_error("vmt_server_create: CUDA resources could not be created");
@@ -479,7 +572,6 @@ int vmt_server_release(vmt_server* s, uint64_t id)
 {
     if (!s) return VMT_EINVAL;
     void* out = nullptr;
-    cudaStream_t fs = nullptr;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         auto it = s->reqs.find(id);
@@ -493,11 +585,10 @@ int vmt_server_release(vmt_server* s, uint64_t id)
             return VMT_EBUSY;
         }
         out = q.out;
-        fs = q.free_stream;
         if (q.admitted) s->used_out -= q.bytes;
         s->reqs.erase(it);
     }
-    if (out) cudaFreeAsync(out, fs);
+    if (out) cudaFreeAsync(out, s->s_free);
     s->cv_work.notify_all();
     return VMT_OK;
 }
@@ -516,6 +607,9 @@ int vmt_server_stats(vmt_server* s, vmt_server_counters* out)
     out->output_bytes_in_use = s->used_out;
     out->peak_state_bytes = s->peak_state;
     out->peak_output_bytes = s->peak_out;
+    out->host_launch_s = s->host_launch_s;
+    out->init_gpu_s = s->init_gpu_s;
+    out->batch_gpu_s = s->batch_gpu_s;
     return VMT_OK;
 }
 
@@ -530,10 +624,12 @@ void vmt_server_destroy(vmt_server* s)
     if (s->worker.joinable()) s->worker.join();
     for (auto& sl : s->slots) {
         if (sl.s_gen) cudaStreamSynchronize(sl.s_gen);
-        if (sl.s_init) cudaStreamSynchronize(sl.s_init);
+        for (cudaStream_t si : sl.s_init)
+            if (si) cudaStreamSynchronize(si);
     }
     for (auto& kv : s->reqs)
-        if (kv.second.out) cudaFreeAsync(kv.second.out, kv.second.free_stream);
+        if (kv.second.out) cudaFreeAsync(kv.second.out, s->s_free);
+    if (s->s_free) cudaStreamSynchronize(s->s_free);
     for (auto& sl : s->slots) {
         if (sl.s_gen) cudaStreamSynchronize(sl.s_gen);
         if (sl.h_units) cudaFreeHost(sl.h_units);
@@ -543,9 +639,16 @@ void vmt_server_destroy(vmt_server* s)
         if (sl.h_jumps) cudaFreeHost(sl.h_jumps);
         if (sl.h_map) cudaFreeHost(sl.h_map);
         if (sl.d_map) cudaFree(sl.d_map);
-        if (sl.s_init) cudaStreamDestroy(sl.s_init);
+        for (cudaEvent_t e : sl.ev)
+            if (e) cudaEventDestroy(e);
+        for (cudaStream_t si : sl.s_init)
+            if (si) cudaStreamDestroy(si);
+        for (cudaEvent_t e : sl.ev_init)
+            if (e) cudaEventDestroy(e);
         if (sl.s_gen) cudaStreamDestroy(sl.s_gen);
     }
+    if (s->s_free) cudaStreamDestroy(s->s_free);
+    if (s->pool) cudaMemPoolDestroy(s->pool);   // its memory is returned once the frees above complete
     delete s;
 }
 

@@ -378,12 +378,22 @@ int ensure_chunks(int variant)
     if (c.chunks_ready) return VMT_OK;
     const uint64_t delta = static_cast<uint64_t>(vmt::kChunkBlocks) * vmt::units_per_lane(variant);
     std::vector<uint32_t> host(static_cast<size_t>(vmt::kChunkRows) * vmt::kPolyWords);
-    const Poly step = c.mod->x_pow(delta);
-    Poly cur = step;
+    // rows 1..T serially, then T threads, thread i taking rows i, i + T, ...
+    // (row j + T = row j * x^(T delta))
+    constexpr int T = 16;
+    std::vector<Poly> rows(static_cast<size_t>(vmt::kChunkRows) + 1);
+    rows[1] = c.mod->x_pow(delta);
+    for (int j = 2; j <= T; ++j) rows[static_cast<size_t>(j)] = c.mod->mul(rows[static_cast<size_t>(j - 1)], rows[1]);
+    std::vector<std::thread> th;
+    for (int i = 1; i <= T; ++i)
+        th.emplace_back([&, i]() {
+            for (int j = i + T; j <= vmt::kChunkRows; j += T)
+                rows[static_cast<size_t>(j)] = c.mod->mul(rows[static_cast<size_t>(j - T)], rows[static_cast<size_t>(T)]);
+        });
+    for (auto& t : th) t.join();
     for (int j = 1; j <= vmt::kChunkRows; ++j) {
-        if (j > 1) cur = c.mod->mul(cur, step);
-        to_rows(cur, &host[static_cast<size_t>(j - 1) * vmt::kPolyWords]);
-        c.row_deg[static_cast<size_t>(kChunkRow0 + j - 1)] = vmt::gf2::degree(cur);
+        to_rows(rows[static_cast<size_t>(j)], &host[static_cast<size_t>(j - 1) * vmt::kPolyWords]);
+        c.row_deg[static_cast<size_t>(kChunkRow0 + j - 1)] = vmt::gf2::degree(rows[static_cast<size_t>(j)]);
     }
     CUDA_TRY(cudaMemcpy(c.d_table + static_cast<size_t>(kChunkRow0) * vmt::kPolyWords, host.data(),
                         host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
@@ -711,93 +721,132 @@ int vmt_set_cache_dir(const char* path)
 
 }  // extern "C"
 
-// Creates the state object; with async_alloc its device memory comes from
-// the stream-ordered pool of cuda_stream (free it with vmt::free_state_async).
-int vmt::init_batch_impl(vmt_state** out, int variant, int lanes, int64_t count, const uint64_t* seeds,
-                         const uint64_t* jumps, void* cuda_stream, bool async_alloc)
+// Creates nsub state objects of one variant (object i: lanes[i] lanes,
+// counts[i] generators, whose seeds and offsets follow those of objects
+// 0..i-1 in seeds/jumps).  Seeding and the jump offsets run once over all
+// generators; the lane fan-out runs per object.  With async_alloc the device
+// memory comes from the stream-ordered pool `pool` (the default pool when
+// null); free such objects with vmt::free_state_async.
+int vmt::init_multi_impl(vmt_state** outs, int variant, int nsub, const int* lanes, const int64_t* counts,
+                         const uint64_t* seeds, const uint64_t* jumps, void* cuda_stream, bool async_alloc,
+                         cudaMemPool_t pool)
 {
-    if (!out) return fail(VMT_EINVAL, "null output handle");
-    *out = nullptr;
+    if (!outs || !lanes || !counts || nsub < 1) return fail(VMT_EINVAL, "null argument");
+    for (int i = 0; i < nsub; ++i) outs[i] = nullptr;
     if (!valid_variant(variant)) return fail(VMT_EINVAL, "bad variant");
-    if (!valid_lanes(lanes)) return fail(VMT_EINVAL, "lanes must be 1, 2, 4, 8 or 16");
-    if (count < 1 || !seeds) return fail(VMT_EINVAL, "count must be >= 1 and seeds non-null");
+    int64_t total = 0;
+    for (int i = 0; i < nsub; ++i) {
+        if (!valid_lanes(lanes[i])) return fail(VMT_EINVAL, "lanes must be 1, 2, 4, 8 or 16");
+        if (counts[i] < 1) return fail(VMT_EINVAL, "count must be >= 1");
+        total += counts[i];
+    }
+    if (!seeds) return fail(VMT_EINVAL, "seeds must be non-null");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     int rc = ensure_variant(variant, s);
     if (rc) return rc;
     bool any_jump = false;
     if (jumps)
-        for (int64_t g = 0; g < count && !any_jump; ++g) any_jump = jumps[g] != 0;
+        for (int64_t g = 0; g < total && !any_jump; ++g) any_jump = jumps[g] != 0;
     if (any_jump && (rc = ensure_digits(variant))) return rc;
     VariantCtx& c = g_ctx[variant];
 
-    std::unique_ptr<vmt_state> st(new vmt_state());
-    st->variant = variant;
-    st->lanes = lanes;
-    st->count = count;
-    CUDA_TRY(cudaGetDevice(&st->device));
-    const int64_t bytes = state_total_bytes(st.get());
-    const int64_t B = vmt::block_words(variant, lanes);
-    bool ok;
-    if (async_alloc) {
-        ok = cudaMallocAsync(&st->d_states, static_cast<size_t>(bytes), s) == cudaSuccess &&
-             cudaMallocAsync(reinterpret_cast<void**>(&st->d_pos), static_cast<size_t>(count) * sizeof(int), s) ==
-                 cudaSuccess;
-        st->async_alloc = true;
-    } else {
-        ok = cudaMalloc(&st->d_states, static_cast<size_t>(bytes)) == cudaSuccess &&
-             cudaMalloc(reinterpret_cast<void**>(&st->d_pos), static_cast<size_t>(count) * sizeof(int)) == cudaSuccess;
+    std::vector<std::unique_ptr<vmt_state>> made;
+    // on any failure below, every object made so far is released
+    auto drop = [&](vmt_state* st) { st->async_alloc ? vmt::free_state_async(st, s) : vmt_free(st); };
+    const int rc_body = [&]() -> int {
+    for (int i = 0; i < nsub; ++i) {
+        std::unique_ptr<vmt_state> st(new vmt_state());
+        st->variant = variant;
+        st->lanes = lanes[i];
+        st->count = counts[i];
+        CUDA_TRY(cudaGetDevice(&st->device));
+        const int64_t bytes = state_total_bytes(st.get());
+        const int64_t B = vmt::block_words(variant, lanes[i]);
+        bool ok;
+        if (async_alloc) {
+            ok = vmt::malloc_async(&st->d_states, static_cast<size_t>(bytes), pool, s) == cudaSuccess &&
+                 vmt::malloc_async(reinterpret_cast<void**>(&st->d_pos), static_cast<size_t>(counts[i]) * sizeof(int),
+                                   pool, s) == cudaSuccess;
+            st->async_alloc = true;
+        } else {
+            ok = cudaMalloc(&st->d_states, static_cast<size_t>(bytes)) == cudaSuccess &&
+                 cudaMalloc(reinterpret_cast<void**>(&st->d_pos), static_cast<size_t>(counts[i]) * sizeof(int)) ==
+                     cudaSuccess;
+        }
+        if (!ok) {
+            cudaGetLastError();
+            drop(st.release());
+            return fail(VMT_ENOMEM, "allocation of " + std::to_string(bytes) + " state bytes failed");
+        }
+        st->h_pos.assign(static_cast<size_t>(counts[i]), B);   // exhausted: the first output twists
+        st->uniform = true;
+        CUDA_TRY(vmt::launch_fill_int(st->d_pos, counts[i], static_cast<int>(B), s));
+        made.push_back(std::move(st));
     }
-    if (!ok) {
-        cudaGetLastError();
-        if (st->d_states) async_alloc ? (void)cudaFreeAsync(st->d_states, s) : (void)cudaFree(st->d_states);
-        return fail(VMT_ENOMEM, "allocation of " + std::to_string(bytes) + " state bytes failed");
-    }
-    st->h_pos.assign(static_cast<size_t>(count), B);   // exhausted: the first output twists
-    st->uniform = true;
-    CUDA_TRY(vmt::launch_fill_int(st->d_pos, count, static_cast<int>(B), s));
     const int n_units = vmt::units_per_lane(variant);
     const int unit_bytes = vmt::word_bytes(variant) * vmt::words_per_unit(variant);
     // scratch: seeds, offsets and the unjumped base states, unit-major [u][g]
     unsigned long long* d_seeds = nullptr;
     unsigned long long* d_jumps = nullptr;
     char* d_base = nullptr;
-    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_seeds), static_cast<size_t>(count) * 8, s));
-    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_base), static_cast<size_t>(count * n_units * unit_bytes), s));
-    CUDA_TRY(cudaMemcpyAsync(d_seeds, seeds, static_cast<size_t>(count) * 8, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(vmt::launch_seed(variant, count, d_seeds, d_base, s));
+    CUDA_TRY(vmt::malloc_async(reinterpret_cast<void**>(&d_seeds), static_cast<size_t>(total) * 8, pool, s));
+    CUDA_TRY(vmt::malloc_async(reinterpret_cast<void**>(&d_base), static_cast<size_t>(total * n_units * unit_bytes),
+                               pool, s));
+    CUDA_TRY(cudaMemcpyAsync(d_seeds, seeds, static_cast<size_t>(total) * 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(vmt::launch_seed(variant, total, d_seeds, d_base, s));
     vmt::JumpGrid gr{};
-    gr.count = count;
-    gr.lanes = lanes;
+    gr.count = total;
     gr.base = d_base;
     gr.unit_bytes = unit_bytes;
-    gr.states = static_cast<char*>(st->d_states);
-    gr.gen_bytes = vmt::state_bytes_per_gen(variant, lanes);
     gr.row_deg = c.d_row_deg;
     if (any_jump) {
         // base <- x^d(F) base, one base-256 digit per launch (jumps commute)
-        CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_jumps), static_cast<size_t>(count) * 8, s));
-        CUDA_TRY(cudaMemcpyAsync(d_jumps, jumps, static_cast<size_t>(count) * 8, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(vmt::malloc_async(reinterpret_cast<void**>(&d_jumps), static_cast<size_t>(total) * 8, pool, s));
+        CUDA_TRY(cudaMemcpyAsync(d_jumps, jumps, static_cast<size_t>(total) * 8, cudaMemcpyHostToDevice, s));
         gr.mode = vmt::JumpGrid::kDigit;
         gr.jumps = d_jumps;
         for (int i = 0; i < 8; ++i) {
             bool used = false;
-            for (int64_t g = 0; g < count && !used; ++g) used = ((jumps[g] >> (8 * i)) & 255u) != 0;
+            for (int64_t g = 0; g < total && !used; ++g) used = ((jumps[g] >> (8 * i)) & 255u) != 0;
             if (!used) continue;
             gr.digit = i;
-            if ((rc = run_jump_grid(variant, gr, count, c.d_table, s))) return rc;
+            if ((rc = run_jump_grid(variant, gr, total, c.d_table, s))) return rc;
         }
     }
-    // lane fan-out: lane t = x^(t J)(F) base, written into X-hat's column t
+    // lane fan-out per object: lane t = x^(t J)(F) base, written into X-hat's
+    // column t (the base keeps its unit stride `total`)
     gr.mode = vmt::JumpGrid::kFanOut;
-    if ((rc = run_jump_grid(variant, gr, count * lanes, c.d_table, s))) return rc;
+    int64_t g0 = 0;
+    for (int i = 0; i < nsub; ++i) {
+        gr.base = d_base + g0 * unit_bytes;
+        gr.lanes = lanes[i];
+        gr.states = static_cast<char*>(made[static_cast<size_t>(i)]->d_states);
+        gr.gen_bytes = vmt::state_bytes_per_gen(variant, lanes[i]);
+        if ((rc = run_jump_grid(variant, gr, counts[i] * lanes[i], c.d_table, s))) return rc;
+        g0 += counts[i];
+    }
     CUDA_TRY(cudaFreeAsync(d_seeds, s));
     CUDA_TRY(cudaFreeAsync(d_base, s));
     if (d_jumps) CUDA_TRY(cudaFreeAsync(d_jumps, s));
-    *out = st.release();
+    return VMT_OK;
+    }();
+    if (rc_body != VMT_OK) {
+        for (auto& m : made) drop(m.release());
+        return rc_body;
+    }
+    for (int i = 0; i < nsub; ++i) outs[i] = made[static_cast<size_t>(i)].release();
     return VMT_OK;
 }
 
-int vmt::alloc_states_async(vmt_state** out, int variant, int lanes, int64_t count, void* cuda_stream)
+int vmt::init_batch_impl(vmt_state** out, int variant, int lanes, int64_t count, const uint64_t* seeds,
+                         const uint64_t* jumps, void* cuda_stream, bool async_alloc, cudaMemPool_t pool)
+{
+    if (!out) return fail(VMT_EINVAL, "null output handle");
+    return vmt::init_multi_impl(out, variant, 1, &lanes, &count, seeds, jumps, cuda_stream, async_alloc, pool);
+}
+
+int vmt::alloc_states_async(vmt_state** out, int variant, int lanes, int64_t count, void* cuda_stream,
+                            cudaMemPool_t pool)
 {
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     std::unique_ptr<vmt_state> st(new vmt_state());
@@ -807,8 +856,9 @@ int vmt::alloc_states_async(vmt_state** out, int variant, int lanes, int64_t cou
     st->async_alloc = true;
     CUDA_TRY(cudaGetDevice(&st->device));
     const int64_t B = vmt::block_words(variant, lanes);
-    if (cudaMallocAsync(&st->d_states, static_cast<size_t>(state_total_bytes(st.get())), s) != cudaSuccess ||
-        cudaMallocAsync(reinterpret_cast<void**>(&st->d_pos), static_cast<size_t>(count) * sizeof(int), s) != cudaSuccess) {
+    if (vmt::malloc_async(&st->d_states, static_cast<size_t>(state_total_bytes(st.get())), pool, s) != cudaSuccess ||
+        vmt::malloc_async(reinterpret_cast<void**>(&st->d_pos), static_cast<size_t>(count) * sizeof(int), pool, s) !=
+            cudaSuccess) {
         cudaGetLastError();
         if (st->d_states) cudaFreeAsync(st->d_states, s);
         return fail(VMT_ENOMEM, "chunk state allocation failed");
@@ -905,6 +955,30 @@ int vmt_jump(vmt_state* st, const uint64_t* poly, int64_t nbits, void* cuda_stre
     CUDA_TRY(cudaFreeAsync(d_row, s));
     // the host vectors were staged by the copies above (pageable memory)
     return VMT_OK;
+}
+
+int vmt_tune_jump_set(int variant, int64_t split_below)
+{
+    if (split_below < 0) return fail(VMT_EINVAL, "split_below must be >= 0");
+    if (variant != -1 && !valid_variant(variant)) return fail(VMT_EINVAL, "bad variant");
+    for (int v = 0; v < 3; ++v)
+        if (variant == -1 || variant == v) vmt::set_jump_split_below(v, split_below);
+    return VMT_OK;
+}
+
+int64_t vmt_tune_jump_get(int variant)
+{
+    if (!valid_variant(variant)) return fail(VMT_EINVAL, "bad variant");
+    return vmt::get_jump_split_below(variant);
+}
+
+int vmt_prepare(int variant, void* cuda_stream)
+{
+    if (!valid_variant(variant)) return fail(VMT_EINVAL, "bad variant");
+    int rc = ensure_variant(variant, static_cast<cudaStream_t>(cuda_stream));
+    if (!rc) rc = ensure_digits(variant);
+    if (!rc) rc = ensure_chunks(variant);
+    return rc;
 }
 
 int vmt_jump_poly(int variant, uint64_t d, int log2_extra, uint64_t* poly_out, int64_t cap_words)

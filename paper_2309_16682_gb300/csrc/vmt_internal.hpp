@@ -108,6 +108,9 @@ cudaError_t launch_seed(int variant, long long count, const unsigned long long* 
 cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s);
 cudaError_t launch_jump_grid(int variant, const JumpGrid& gr, long long nitems, const uint32_t* polys, cudaStream_t s);
 cudaError_t launch_fill_int(int* p, long long n, int value, cudaStream_t s);
+// jump launches of fewer items than `items` run one CTA per item
+void set_jump_split_below(int variant, long long items);
+long long get_jump_split_below(int variant);
 
 }  // namespace vmt
 
@@ -137,14 +140,27 @@ namespace vmt {
 int launch_unit_table(int variant, int lanes, int dtype, const UnitDesc* d_units, int64_t n, int* counter,
                       void* stream);
 
-// state creation with optional stream-ordered allocation, and its release
+// stream-ordered allocation from `pool`, or from the device's default pool
+// when pool is null
+inline cudaError_t malloc_async(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t s)
+{
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+}
+
+// state creation with optional stream-ordered allocation (from `pool` when
+// given), and its release
 int init_batch_impl(vmt_state** out, int variant, int lanes, int64_t count, const uint64_t* seeds,
-                    const uint64_t* jumps, void* cuda_stream, bool async_alloc);
+                    const uint64_t* jumps, void* cuda_stream, bool async_alloc, cudaMemPool_t pool = nullptr);
+// several objects of one variant: seeding and offsets once, fan-out per object
+int init_multi_impl(vmt_state** outs, int variant, int nsub, const int* lanes, const int64_t* counts,
+                    const uint64_t* seeds, const uint64_t* jumps, void* cuda_stream, bool async_alloc,
+                    cudaMemPool_t pool = nullptr);
 void free_state_async(vmt_state* st, void* cuda_stream);
 
 // `count` generators with unset states (to be written by a jump), fresh
 // positions, stream-ordered memory
-int alloc_states_async(vmt_state** out, int variant, int lanes, int64_t count, void* cuda_stream);
+int alloc_states_async(vmt_state** out, int variant, int lanes, int64_t count, void* cuda_stream,
+                       cudaMemPool_t pool = nullptr);
 
 // chunk states: chunk k = row (chunk_map[k].y) applied to every lane of
 // request chunk_map[k].x of `requests`; d_map on the device

@@ -49,6 +49,7 @@ def test_invalid_arguments_rejected(L):
     assert b"lanes" in L.vmt_last_error() or b"count" in L.vmt_last_error()
     assert L.vmt_generate(None, 10, 0, None, None) == vmt.VMT_EINVAL
     assert L.vmt_state_import(None, None, 0, None) == vmt.VMT_EINVAL
+    assert L.vmt_prepare(3, None) == vmt.VMT_EINVAL
 
 
 @pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])

@@ -279,3 +279,45 @@ def test_batch_and_graph_match_plain_calls(vmt):
             assert np.array_equal(got[k], ref), (rnd, k)
     b.close()
     assert vmt.device_status() == 0
+
+
+@pytest.fixture
+def jump_kernel_mode(vmt, request):
+    """Force every jump launch onto one kernel: 'split' (one CTA per
+    lane-jump) or 'warp' (one warp per lane-jump)."""
+    value = 1 << 40 if request.param == "split" else 0
+    old = {v: vmt.tune_jump(v, value) for v in ("mt32", "mt64", "sfmt")}
+    yield request.param
+    for v, x in old.items():
+        vmt.tune_jump(v, x)
+
+
+@pytest.mark.parametrize("jump_kernel_mode", ["split", "warp"], indirect=True)
+@pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])
+def test_both_jump_kernels_match_oracle(vmt, oracle_polys, variant, jump_kernel_mode):
+    """Seeding, 64-bit offsets (all eight base-256 digits), lane fan-out and a
+    random jump polynomial of degree near the state size, each jump kernel
+    against the oracle."""
+    M = 8
+    seeds = np.array([7, 8, 9, 10, 11], np.uint64)
+    jumps = np.array([0, 1, 255, 0x0123456789ABCDEF, 2**64 - 1], np.uint64)
+    g = vmt.VGenerator(VNAME[variant], M, seeds, jumps)
+    native = "u64" if variant == O.MT64 else "u32"
+    wpo = O.words_per_output(variant, native)
+    n0 = 700
+    got0 = _np(g.generate(n0, native))
+    nbits = 19900
+    poly = np.random.default_rng(17 + variant).integers(0, 2**63, size=312, dtype=np.uint64)
+    poly[nbits // 64] &= np.uint64((1 << (nbits % 64)) - 1)
+    poly[nbits // 64 + 1:] = 0
+    poly[0] |= np.uint64(1)
+    g.jump(poly, nbits=nbits)
+    got1 = _np(g.generate(n0, native))
+    for gi in range(seeds.size):
+        lanes = O.lane_states(variant, M, int(seeds[gi]), int(jumps[gi]))
+        ref0 = O.vstream_words(variant, M, 0, n0 * wpo, 0, lanes=lanes)
+        _assert_same(got0[gi], O.convert(variant, ref0, native), f"{jump_kernel_mode} init g{gi}")
+        # the jump advances every lane's state; the position inside the block stays
+        jl = [O.jump(st, poly) for st in lanes]
+        ref1 = O.vstream_words(variant, M, 0, 2 * n0 * wpo, 0, lanes=jl)
+        _assert_same(got1[gi], O.convert(variant, ref1[n0 * wpo:], native), f"{jump_kernel_mode} jump g{gi}")

@@ -150,3 +150,20 @@ def test_chunk_boundary_matches_oracle(vmt, oracle_polys):
     assert np.array_equal(got[C - 700:], ref)
     srv.release(rid)
     srv.close()
+
+
+def test_reserved_pool_and_counters(vmt):
+    srv = vmt.Server(state_budget=1 << 26, output_budget=1 << 28, max_batch=8, reserve=True)
+    ids = [srv.submit("mt32", 8, "u32", s, s, 300_000) for s in range(6)]
+    for rid, s in zip(ids, range(6)):
+        srv.wait(rid)
+        assert np.array_equal(srv.copy(rid, "u32"), _alone(vmt, "mt32", 8, "u32", s, s, 300_000))
+        srv.release(rid)
+    st = srv.stats()
+    assert st["completed"] == 6 and st["batches"] >= 1
+    assert st["host_launch_s"] > 0 and 0 < st["init_gpu_s"] <= st["batch_gpu_s"]
+    srv.close()
+    free, _ = torch.cuda.mem_get_info()
+    with pytest.raises(vmt.VMTError) as ei:   # budgets larger than the device: creation fails cleanly
+        vmt.Server(state_budget=1 << 30, output_budget=4 * free, max_batch=8, reserve=True)
+    assert ei.value.code == vmt.VMT_ENOMEM
