@@ -131,19 +131,13 @@ def dist_setup(n_gpus: int):
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2309_16682_gb300 import shard
+    shard.barrier()
 
 
 def max_over_ranks(world, x: float) -> float:
-    if world <= 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2309_16682_gb300 import shard
+    return shard.max_over_ranks(x)
 
 
 # ---------------------------------------------------------------------------
@@ -317,9 +311,10 @@ def run_gb300(args, world, rank, local):
     count = args.generators or w["generators"]
     esize = {"u32": 4, "f32": 4, "u64": 8, "f64": 8}
     out_bytes = sum(n * count * esize[dt] for n, dt in segs)
-    seeds = I.workload_seeds(args.workload)[:count]
-    if rank:
-        seeds = I.splitmix64(1000003 * rank + 1, count)  # each rank: its own generators
+    # rank r owns generators [r * count, (r + 1) * count) of the workload's
+    # global generator sequence (weak scaling, no collective on the data path)
+    from paper_2309_16682_gb300 import shard
+    seeds = shard.rank_seeds(args.workload, world, rank, count)
     stream = torch.cuda.current_stream()
 
     # one-time initialisation: seeding + jump-ahead de-phasing (timed separately)

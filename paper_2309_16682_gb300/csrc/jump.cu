@@ -27,6 +27,7 @@
 #include <atomic>
 
 #include "vmt_device.cuh"
+#include "vmt_internal.hpp"
 
 namespace vmt {
 namespace dev {

@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "vmt_device.cuh"
+#include "vmt_internal.hpp"
 
 namespace {
 

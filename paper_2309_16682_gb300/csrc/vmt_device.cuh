@@ -20,7 +20,9 @@
 #pragma once
 #include <cstdint>
 
-#include "vmt_internal.hpp"
+#include <cuda_runtime.h>
+
+#include "gen_args.hpp"
 
 namespace vmt {
 namespace dev {

@@ -37,10 +37,11 @@ def splitmix64_scalar(state: int, count: int) -> list[int]:
     return out
 
 
-def splitmix64(state: int, count: int) -> np.ndarray:
-    """Vectorised form: the i-th output only depends on state + (i+1)*GOLDEN."""
+def splitmix64(state: int, count: int, first: int = 0) -> np.ndarray:
+    """Vectorised form: the i-th output only depends on state + (i+1)*GOLDEN,
+    so outputs [first, first + count) come without the ones before them."""
     with np.errstate(over="ignore"):
-        i = np.arange(1, count + 1, dtype=np.uint64)
+        i = np.arange(first + 1, first + count + 1, dtype=np.uint64)
         s = np.uint64(state & MASK64) + i * np.uint64(GOLDEN)
         z = (s ^ (s >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
         z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
@@ -68,14 +69,18 @@ WORKLOADS = {
 }
 
 
-def workload_seeds(name: str) -> np.ndarray:
+def workload_seeds(name: str, first: int = 0, count: int | None = None) -> np.ndarray:
+    """Seeds of generators [first, first + count) of the workload's global
+    generator sequence (count defaults to the workload's generator count).
+    With several GPUs each rank takes its own slice of the same sequence."""
     w = WORKLOADS[name]
+    n = w["generators"] if count is None else count
     if w["seed_mode"] == "fixed":
-        return np.full(w["generators"], w["seed"], dtype=np.uint64)
+        return np.full(n, w["seed"], dtype=np.uint64)
     if w["seed_mode"] == "consecutive":
         # generator g is seeded with seed + g, so generator 0 keeps the named seed
-        return np.uint64(w["seed"]) + np.arange(w["generators"], dtype=np.uint64)
-    return splitmix64(w["seed"], w["generators"])
+        return np.uint64(w["seed"]) + np.arange(first, first + n, dtype=np.uint64)
+    return splitmix64(w["seed"], n, first)
 
 
 def request_trace(count: int, rate_per_s: float = 2.0e4, seed: int = 2,

@@ -321,3 +321,14 @@ def test_both_jump_kernels_match_oracle(vmt, oracle_polys, variant, jump_kernel_
         jl = [O.jump(st, poly) for st in lanes]
         ref1 = O.vstream_words(variant, M, 0, 2 * n0 * wpo, 0, lanes=jl)
         _assert_same(got1[gi], O.convert(variant, ref1[n0 * wpo:], native), f"{jump_kernel_mode} jump g{gi}")
+
+
+def test_two_shards_equal_one_run(vmt):
+    """Generators split over two objects (as over two ranks) give the same
+    outputs as one object holding all of them."""
+    from paper_2309_16682_gb300 import shard
+    name, per = "vmt32_m16_g65536", 96
+    seeds = shard.rank_seeds(name, 1, 0, 2 * per)
+    whole = _np(vmt.VGenerator("mt32", 16, seeds).generate(5000, "u32"))
+    parts = [_np(vmt.VGenerator("mt32", 16, shard.rank_seeds(name, 2, r, per)).generate(5000, "u32")) for r in range(2)]
+    assert np.array_equal(np.concatenate(parts), whole)
