@@ -186,6 +186,48 @@ def oracle_sample(workload: str, min_seconds: float, max_gens: int = 1 << 20):
     return nbytes, time.perf_counter() - t0, gens
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_worker(workload, seconds, barrier, q):
+    """One host process of the all-cores oracle timing: prepare untimed, meet
+    the others at the barrier, then produce for `seconds`."""
+    try:
+        import oracle as O
+        O.prepare_all()
+        _oracle_pool(workload)
+        oracle_sample(workload, 0.0, max_gens=1)
+        barrier.wait(timeout=300)
+        b, t, gens = oracle_sample(workload, seconds)
+        q.put((b, t, gens))
+    except Exception as e:  # reported to the parent
+        q.put(("error", repr(e), 0))
+
+
+def oracle_sample_procs(workload: str, seconds: float, procs: int):
+    """oracle_sample in `procs` host processes at once (spawned, so safe after
+    GPU work); returns (bytes, seconds of the slowest, generators)."""
+    import multiprocessing as mp
+    import oracle as O
+    O.prepare_all()                       # polynomial caches written before the workers read them
+    ctx = mp.get_context("spawn")
+    barrier, q = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(workload, seconds, barrier, q)) for _ in range(procs)]
+    for p in ps:
+        p.start()
+    res = [q.get(timeout=600) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+    bad = [r for r in res if r[0] == "error"]
+    if bad:
+        raise RuntimeError(f"oracle worker failed: {bad[0][1]}")
+    return sum(r[0] for r in res), max(r[1] for r in res), sum(r[2] for r in res)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -195,21 +237,23 @@ def run_reference(args, world, rank):
     _oracle_pool(args.workload)
     for _ in range(args.warmup):
         oracle_sample(args.workload, 0.0, max_gens=1)
+    cores = host_cores()
     tot_b, tot_t, tot_g = 0, 0.0, 0
     for _ in range(args.steps):
-        b, t, gens = oracle_sample(args.workload, args.ref_seconds / max(args.steps, 1))
+        b, t, gens = oracle_sample_procs(args.workload, args.ref_seconds / max(args.steps, 1), cores)
         tot_b += b
         tot_t += t
         tot_g += gens
     val = tot_b / tot_t / 1e9
     sample = (f"{tot_g} whole per-generator step outputs ({tot_b} bytes) of the {w['generators']}-generator "
-              f"workload over {args.steps} steps; lane states from a pool of 4 generators prepared untimed")
+              f"workload over {args.steps} steps on {cores} host processes; lane states from a pool of 4 "
+              f"generators prepared untimed")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "config": {"workload": args.workload},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -317,7 +361,9 @@ def run_gb300(args, world, rank, local):
     seeds = shard.rank_seeds(args.workload, world, rank, count)
     stream = torch.cuda.current_stream()
 
-    # one-time initialisation: seeding + jump-ahead de-phasing (timed separately)
+    # one-time initialisation: seeding + jump-ahead de-phasing (timed
+    # separately, after the variant's polynomial tables are built)
+    vmt.prepare(w["variant"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g = vmt.VGenerator(w["variant"], w["lanes"], seeds)
@@ -338,6 +384,8 @@ def run_gb300(args, world, rank, local):
     def step():
         g.generate_multi(segs, outs=outs)
 
+    # the HBM write ceiling of this GPU (store-only kernel), untimed
+    write_peak = vmt.measure_store_bw(8 << 30, 5)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -381,6 +429,39 @@ def run_gb300(args, world, rank, local):
                "d2h_bytes_per_step": out_bytes, "steps": e2e_steps}
         del hosts
 
+    # jump evaluation (a3) at full size: every lane of every generator by one
+    # full-degree polynomial x^d mod mu, d a 64-bit offset
+    jump = None
+    if not args.no_jump:
+        d = int(I.splitmix64(7, 1)[0])
+        jp = vmt.jump_poly(w["variant"], d)
+        poly = np.zeros(312, np.uint64)          # degree < 19968 for every variant
+        poly[:min(312, jp.size)] = jp[:312]
+        nbits = 312 * 64
+        g.jump(poly, nbits)                 # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            g.jump(poly, nbits)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        jt = e0.elapsed_time(e1) / 1e3 / reps
+        pop = int(sum(bin(int(x)).count("1") for x in poly))
+        # 32-bit XOR-words per lane-jump: set coefficients x lane-state words
+        lane_words = {"mt32": 624, "mt64": 624, "sfmt": 624}[w["variant"]]
+        xw = count * w["lanes"] * pop * lane_words / jt
+        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        alu_peak = sms * 64 * sm_mhz * 1e6
+        jump = {"lane_jumps": count * w["lanes"], "seconds": jt, "lane_jumps_per_s": count * w["lanes"] / jt,
+                "poly_popcount": pop, "xor_words_per_s": xw, "alu_peak_lop3_per_s": alu_peak,
+                "frac": xw / alu_peak, "bound": "alu",
+                "note": "vmt_jump of every lane by x^d mod mu (d a 64-bit offset); 32-bit XOR-words = set "
+                        "coefficients x 624 words per lane-state; peak = SMs x 64 LOP3 lanes/clk x SM clock; "
+                        "a three-input XOR covers two set coefficients, so frac can exceed the pipe's share"}
+
     served = None
     if not args.no_serve:
         served = run_served(vmt, args.serve_requests, 2.0e4, args.plain_requests)
@@ -390,10 +471,14 @@ def run_gb300(args, world, rank, local):
         import oracle as O
         O.prepare_all()
         _, t_pool, pool = _oracle_pool(args.workload)
-        b, t, gens = oracle_sample(args.workload, args.ref_seconds)
-        cpu = {"value": b / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{gens} whole per-generator step outputs ({b} bytes) in {t:.1f} s on one core; "
-                         f"seed+jump of {pool} generators took {t_pool:.1f} s"}
+        cores = host_cores()
+        b, t, gens = oracle_sample_procs(args.workload, 0.6 * args.ref_seconds, cores)
+        b1, t1, g1 = oracle_sample(args.workload, 0.4 * args.ref_seconds)
+        cpu = {"value": b / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "single_core_value": b1 / t1 / 1e9,
+               "sample": f"{gens} whole per-generator step outputs ({b} bytes) in {t:.1f} s on {cores} host "
+                         f"processes, and {g1} in one process in {t1:.1f} s; seed+jump of {pool} generators took "
+                         f"{t_pool:.1f} s (untimed)"}
 
     if rank == 0:
         lane_jumps = count * w["lanes"]
@@ -408,6 +493,7 @@ def run_gb300(args, world, rank, local):
                        "parallelism": f"{world} independent GPU(s), generators sharded, no collective"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
+                         "write_peak": write_peak, "frac_of_write_peak": achieved / write_peak,
                          "traffic": (profiled_traffic(traffic_key) * count / w["generators"]
                                      if profiled_traffic(traffic_key) is not None else None),
                          "peak_kind": peak_kind,
@@ -420,8 +506,9 @@ def run_gb300(args, world, rank, local):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "init": {"seconds": init_s, "lane_jumps": lane_jumps, "lane_jumps_per_s": lane_jumps / init_s,
-                     "note": "seed + jump-ahead de-phasing before the timed region (first call also loads or "
-                             "computes the jump polynomials)"},
+                     "note": "seed + jump-ahead de-phasing of all generators before the timed region (the "
+                             "variant's polynomial tables prepared first, untimed)"},
+            "jump": jump,
             "clocks": clocks,
             "served": served,
         }
@@ -438,6 +525,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--tune", action="store_true", help="run the autotuner before timing")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-mix measurement")
+    ap.add_argument("--no-jump", action="store_true", help="skip the full-size jump measurement")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--plain-requests", type=int, default=1000)
     ap.add_argument("--generators", type=int, default=0,

@@ -290,6 +290,17 @@ int vmt_tune_get(int variant, int lanes);
  */
 int vmt_tune_jump_set(int variant, int64_t split_below);
 int64_t vmt_tune_jump_get(int variant);
+
+/*
+ * vmt_measure_store_bw -- diagnostic, no paper counterpart: the device's HBM
+ * write bandwidth as seen by a store-only kernel (16-byte streaming stores
+ * over `bytes` bytes of a buffer it allocates and frees on cuda_stream), best
+ * of `reps` timed launches per launch shape, in GB/s (10^9 bytes/s).  It is
+ * the ceiling for kernels that mostly write.  Synchronises cuda_stream.
+ * VMT_EINVAL for bytes < 1 MiB, reps < 1 or a null output; VMT_ENOMEM when
+ * the buffer cannot be allocated.
+ */
+int vmt_measure_store_bw(int64_t bytes, int reps, double* best_gbs, void* cuda_stream);
 int vmt_autotune(int variant, int lanes, int64_t count, int64_t n_per_gen, int dtype, int reps, void* cuda_stream,
                  int* best_threads, double* best_ms);
 

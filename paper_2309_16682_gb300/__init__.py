@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "vmt_tune_set": (I, [I, I, I]),
             "vmt_tune_get": (I, [I, I]),
             "vmt_tune_jump_set": (I, [I, I64]),
+            "vmt_measure_store_bw": (I, [I64, I, P, P]),
             "vmt_tune_jump_get": (I64, [I]),
             "vmt_autotune": (I, [I, I, I64, I64, I, I, P, P, P]),
         }
@@ -362,6 +363,13 @@ def autotune(variant: str, lanes: int, count: int, n_per_gen: int, dtype: str = 
     _check(lib().vmt_autotune(VARIANTS[variant], int(lanes), int(count), int(n_per_gen), DTYPES[dtype], int(reps),
                               _stream_handle(stream), ctypes.byref(t), ctypes.byref(ms)))
     return t.value, ms.value
+
+
+def measure_store_bw(nbytes: int = 8 << 30, reps: int = 5, stream=None) -> float:
+    """HBM write bandwidth of a store-only kernel, GB/s (best of reps)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().vmt_measure_store_bw(int(nbytes), int(reps), ctypes.byref(out), _stream_handle(stream)))
+    return out.value
 
 
 def prepare(variant: str, stream=None) -> None:

@@ -50,6 +50,8 @@ def test_invalid_arguments_rejected(L):
     assert L.vmt_generate(None, 10, 0, None, None) == vmt.VMT_EINVAL
     assert L.vmt_state_import(None, None, 0, None) == vmt.VMT_EINVAL
     assert L.vmt_prepare(3, None) == vmt.VMT_EINVAL
+    assert L.vmt_measure_store_bw(1024, 1, None, None) == vmt.VMT_EINVAL
+    assert L.vmt_tune_jump_set(5, 10) == vmt.VMT_EINVAL
 
 
 @pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])
