@@ -462,6 +462,29 @@ def run_gb300(args, world, rank, local):
                         "coefficients x 624 words per lane-state; peak = SMs x 64 LOP3 lanes/clk x SM clock; "
                         "a three-input XOR covers two set coefficients, so frac can exceed the pipe's share"}
 
+    # exact single-stream mode: 2^30 outputs of ONE base generator of the
+    # workload's variant (its own scalar stream), in parallel chunks
+    single = None
+    if not args.no_stream:
+        native = {"mt32": "u32", "mt64": "u64", "sfmt": "u32"}[w["variant"]]
+        ns = 1 << 30 if native == "u32" else 1 << 29
+        sbuf = torch.empty(ns, dtype=vmt._torch_dtype(native), device="cuda")
+        vmt.stream_generate(w["variant"], 5489, ns, native, out=sbuf)   # warm-up (polynomials cached)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            vmt.stream_generate(w["variant"], 5489, ns, native, out=sbuf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st_s = e0.elapsed_time(e1) / 1e3 / reps
+        single = {"value": ns * sbuf.element_size() / st_s / 1e9, "unit": UNIT, "outputs": ns, "dtype": native,
+                  "seconds": st_s, "note": "vmt_stream_generate: one base generator (seed 5489) cut into "
+                                           "jump-started chunks; includes seeding, the chunk jumps and the "
+                                           "generation"}
+        del sbuf
+
     served = None
     if not args.no_serve:
         served = run_served(vmt, args.serve_requests, 2.0e4, args.plain_requests)
@@ -509,6 +532,7 @@ def run_gb300(args, world, rank, local):
                      "note": "seed + jump-ahead de-phasing of all generators before the timed region (the "
                              "variant's polynomial tables prepared first, untimed)"},
             "jump": jump,
+            "single_stream": single,
             "clocks": clocks,
             "served": served,
         }
@@ -526,6 +550,7 @@ def main():
     ap.add_argument("--tune", action="store_true", help="run the autotuner before timing")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-mix measurement")
     ap.add_argument("--no-jump", action="store_true", help="skip the full-size jump measurement")
+    ap.add_argument("--no-stream", action="store_true", help="skip the single-stream measurement")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--plain-requests", type=int, default=1000)
     ap.add_argument("--generators", type=int, default=0,

@@ -292,6 +292,25 @@ int vmt_tune_jump_set(int variant, int64_t split_below);
 int64_t vmt_tune_jump_get(int variant);
 
 /*
+ * vmt_stream_generate -- exact single-stream mode: the first n outputs, from
+ * offset `jump`, of ONE base generator (MT19937-32, MT19937-64 or SFMT19937
+ * as in Sec. 2, seeded as vmt_init with M = 1), i.e. the scalar generator's
+ * own stream (std::mt19937, std::mt19937_64, SFMT19937's 32-bit output
+ * sequence), written to out_dev (n elements).  It is produced in parallel:
+ * the stream is cut into up to 2048 chunks of equal length, chunk j starting
+ * from the base state jumped by j chunk lengths with the polynomial jump-ahead
+ * of Sec. 3.1, and the chunks are generated concurrently.  `jump` counts
+ * steps of the recurrence (SFMT: 128-bit elements, 4 outputs each).
+ * dtype: VMT_U32 or VMT_F32 for the 32-bit generators; VMT_U64, VMT_F64 or
+ * VMT_F32 for MT19937-64 (one output per generator word).  n <= 2^39.
+ * Asynchronous on cuda_stream; all scratch is stream-ordered and released
+ * before the call returns (in stream order).  VMT_EINVAL for a bad variant,
+ * type, n or a null output.
+ */
+int vmt_stream_generate(int variant, uint64_t seed, uint64_t jump, int64_t n, int dtype, void* out_dev,
+                        void* cuda_stream);
+
+/*
  * vmt_measure_store_bw -- diagnostic, no paper counterpart: the device's HBM
  * write bandwidth as seen by a store-only kernel (16-byte streaming stores
  * over `bytes` bytes of a buffer it allocates and frees on cuda_stream), best

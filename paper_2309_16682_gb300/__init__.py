@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
             "vmt_tune_get": (I, [I, I]),
             "vmt_tune_jump_set": (I, [I, I64]),
             "vmt_measure_store_bw": (I, [I64, I, P, P]),
+            "vmt_stream_generate": (I, [I, U64, U64, I64, I, P, P]),
             "vmt_tune_jump_get": (I64, [I]),
             "vmt_autotune": (I, [I, I, I64, I64, I, I, P, P, P]),
         }
@@ -363,6 +364,17 @@ def autotune(variant: str, lanes: int, count: int, n_per_gen: int, dtype: str = 
     _check(lib().vmt_autotune(VARIANTS[variant], int(lanes), int(count), int(n_per_gen), DTYPES[dtype], int(reps),
                               _stream_handle(stream), ctypes.byref(t), ctypes.byref(ms)))
     return t.value, ms.value
+
+
+def stream_generate(variant: str, seed: int, n: int, dtype: str = "u32", jump: int = 0, out=None, stream=None):
+    """The base generator's own stream (M = 1) from offset `jump`, n outputs,
+    generated in parallel chunks (vmt_stream_generate)."""
+    import torch
+    if out is None:
+        out = torch.empty(max(int(n), 1), dtype=_torch_dtype(dtype), device="cuda")[:int(n)]
+    _check(lib().vmt_stream_generate(VARIANTS[variant], int(seed) & (2**64 - 1), int(jump) & (2**64 - 1), int(n),
+                                     DTYPES[dtype], ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out
 
 
 def measure_store_bw(nbytes: int = 8 << 30, reps: int = 5, stream=None) -> float:

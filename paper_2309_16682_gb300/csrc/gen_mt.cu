@@ -600,11 +600,168 @@ int read_generate_timeout(bool reset)
     return v;
 }
 
+namespace dev {
+// ---------------------------------------------------------------------------
+// M = 1: one warp per generator
+// ---------------------------------------------------------------------------
+// A single-lane generator (the base generator's own stream) has only n - m
+// independent words per phase, too few to share a CTA's threads between
+// barriers.  Here a warp owns one generator: its two state copies (2 n words)
+// in shared memory, phases of eq. stepnomod separated by __syncwarp, lane i
+// handling words i, i + 32, ... and storing them coalesced (one output per
+// generator word).
+constexpr int kM1Warps = 8;
+
+template <class G, int DT>
+__device__ __forceinline__ void m1_store(char* out, long long e, typename G::W z)
+{
+    if constexpr (sizeof(typename G::W) == 4) {
+        if constexpr (DT == VMT_U32) __stcs(reinterpret_cast<unsigned int*>(out) + e, z);
+        else __stcs(reinterpret_cast<float*>(out) + e, f32_of_u32(z));
+    } else {
+        if constexpr (DT == VMT_U64) __stcs(reinterpret_cast<unsigned long long*>(out) + e, z);
+        else if constexpr (DT == VMT_F64) __stcs(reinterpret_cast<double*>(out) + e, f64_of_u64(z));
+        else __stcs(reinterpret_cast<float*>(out) + e, f32_of_u64(z));
+    }
+}
+
+// new words [K0, K1) of the block: x_k from the old copy (cur) and, beyond
+// the old copy, from the new one (nxt); call word e + k for k < hi
+template <class G, int DT, int K0, int K1>
+__device__ __forceinline__ void m1_phase(const typename G::W* __restrict__ cur, typename G::W* __restrict__ nxt,
+                                         char* __restrict__ out, long long e, int hi, int lane)
+{
+    constexpr int N = G::N, MM = G::MM;
+    // the two copies never alias, so the loads of several words can be
+    // issued ahead of the stores (unrolled)
+#pragma unroll 4
+    for (int k = K0 + lane; k < K1; k += 32) {
+        const typename G::W x = G::twist(cur[k], k + 1 < N ? cur[k + 1] : nxt[0], k + MM < N ? cur[k + MM] : nxt[k + MM - N]);
+        nxt[k] = x;
+        if (k < hi) m1_store<G, DT>(out, e + k, G::temper(x));
+    }
+}
+
+template <class G, int DT, bool UNITS>
+__global__ void __launch_bounds__(kM1Warps * 32) gen_mt1_kernel(GenArgs a)
+{
+    using W = typename G::W;
+    constexpr int N = G::N, NM = N - G::MM;
+    static_assert(N <= 3 * NM, "at most three phases");
+    __shared__ __align__(16) W bufs[kM1Warps][2][N];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long cursor = static_cast<long long>(blockIdx.x) * kM1Warps + warp;
+    auto take = [&]() -> long long {
+        if (UNITS && a.work_counter) {
+            int u = 0;
+            if (lane == 0) u = atomicAdd(a.work_counter, 1);
+            return static_cast<long long>(__shfl_sync(0xFFFFFFFFu, u, 0));
+        }
+        const long long u = cursor;
+        cursor += static_cast<long long>(gridDim.x) * kM1Warps;
+        return u;
+    };
+    constexpr int esize = (DT == VMT_U32 || DT == VMT_F32) ? 4 : 8;
+    for (long long gi = take(); gi < a.gens; gi = take()) {
+        W* gst;
+        int* posp;
+        long long total;
+        char* out;
+        int p;
+        if constexpr (UNITS) {
+            const UnitDesc& ud = a.units[gi];
+            gst = reinterpret_cast<W*>(ud.state);
+            posp = ud.pos;
+            total = ud.total;
+            out = ud.out;
+            p = *posp;
+        } else {
+            gst = reinterpret_cast<W*>(a.states) + gi * N;
+            posp = a.pos_dev + gi;
+            total = a.total;
+            out = a.seg[0].out + (a.gen0 + gi) * a.seg[0].count * esize;
+            p = a.pos;
+        }
+        W* cur = bufs[warp][0];
+        W* nxt = bufs[warp][1];
+        for (int k = lane; k < N; k += 32) cur[k] = gst[k];
+        __syncwarp();
+        long long e = 0;
+        int final_pos = p;
+        if (p < N && total > 0) {
+            // rest of the current block: block word k is call word k - p
+            const int hi = static_cast<int>(min(static_cast<long long>(N), p + total));
+            for (int k = p + lane; k < hi; k += 32) m1_store<G, DT>(out, k - p, G::temper(cur[k]));
+            e = hi - p;
+            final_pos = hi;
+        }
+        while (e < total) {
+            const int hi = static_cast<int>(min(static_cast<long long>(N), total - e));
+            m1_phase<G, DT, 0, NM>(cur, nxt, out, e, hi, lane);
+            __syncwarp();
+            m1_phase<G, DT, NM, (2 * NM < N ? 2 * NM : N)>(cur, nxt, out, e, hi, lane);
+            __syncwarp();
+            if constexpr (2 * NM < N) {
+                m1_phase<G, DT, (2 * NM < N ? 2 * NM : N), N>(cur, nxt, out, e, hi, lane);
+                __syncwarp();
+            }
+            W* t = cur;
+            cur = nxt;
+            nxt = t;
+            e += hi;
+            final_pos = hi;
+        }
+        for (int k = lane; k < N; k += 32) gst[k] = cur[k];
+        if (lane == 0) *posp = final_pos;
+        __syncwarp();
+    }
+}
+
+template <class G, int DT, bool UNITS>
+static cudaError_t launch_mt1_t(const GenArgs& a, cudaStream_t st)
+{
+    long long grid = (a.gens + kM1Warps - 1) / kM1Warps;
+    if (UNITS && a.work_counter) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long persistent = static_cast<long long>(sms) * 5;   // 40 KB of shared memory per CTA
+        if (grid > persistent) grid = persistent;
+    }
+    if (grid > (1LL << 30)) grid = 1LL << 30;
+    gen_mt1_kernel<G, DT, UNITS><<<static_cast<unsigned>(grid), kM1Warps * 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class G, int DT>
+static cudaError_t launch_mt1(const GenArgs& a, cudaStream_t st)
+{
+    if (a.gens <= 0) return cudaSuccess;
+    return a.units ? launch_mt1_t<G, DT, true>(a, st) : launch_mt1_t<G, DT, false>(a, st);
+}
+
+// true when the warp kernel takes the call: one segment from word 0 of a type
+// that takes one generator word per output
+static bool m1_eligible(int variant, const GenArgs& a)
+{
+    if (a.nseg != 1 || a.seg[0].wbeg != 0) return false;
+    const int d = a.seg[0].dtype;
+    return variant == VMT_MT19937_64 ? (d == VMT_U64 || d == VMT_F64 || d == VMT_F32) : (d == VMT_U32 || d == VMT_F32);
+}
+}  // namespace dev
+
 cudaError_t launch_generate_mt(int variant, int lanes, const GenArgs& a, cudaStream_t s)
 {
     using namespace dev;
     // a.threads selects among the compiled CTA sizes (0: default)
     const int t = a.threads;
+    if (lanes == 1 && m1_eligible(variant, a)) {
+        const int d = a.seg[0].dtype;
+        if (variant == VMT_MT19937_32)
+            return d == VMT_U32 ? launch_mt1<MT32, VMT_U32>(a, s) : launch_mt1<MT32, VMT_F32>(a, s);
+        return d == VMT_U64 ? launch_mt1<MT64, VMT_U64>(a, s)
+                            : (d == VMT_F64 ? launch_mt1<MT64, VMT_F64>(a, s) : launch_mt1<MT64, VMT_F32>(a, s));
+    }
     if (variant == VMT_MT19937_32) {
         switch (lanes) {
         case 1: return launch_mt<MT32, 1, 1, 256>(a, s);

@@ -957,6 +957,136 @@ int vmt_jump(vmt_state* st, const uint64_t* poly, int64_t nbits, void* cuda_stre
     return VMT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// exact single-stream mode
+// ---------------------------------------------------------------------------
+// One base generator's stream (M = 1) cut into P chunks of equal length; chunk
+// j's state is the base state advanced by j chunk lengths.  The chunk states
+// come from a doubling tree of jumps (Sec. 3.1): at level k, chunk j in
+// [2^k, 2^(k+1)) is chunk j - 2^k jumped by x^(2^k * steps), so only the
+// polynomials x^(2^k * steps) mod mu, k < log2 P, are needed (one power, then
+// squarings; cached per variant and chunk length).
+namespace {
+struct StreamPolys {
+    uint64_t steps = 0;
+    std::vector<Poly> rows;
+};
+std::mutex g_stream_mu;
+StreamPolys g_stream_polys[3];
+
+void stream_polys(int variant, uint64_t steps, int levels, std::vector<Poly>& out)
+{
+    VariantCtx& c = g_ctx[variant];
+    std::lock_guard<std::mutex> lk(g_stream_mu);
+    StreamPolys& sp = g_stream_polys[variant];
+    if (sp.steps != steps) {
+        sp.steps = steps;
+        sp.rows.clear();
+    }
+    if (sp.rows.empty()) sp.rows.push_back(c.mod->x_pow(steps));
+    while (static_cast<int>(sp.rows.size()) < levels) sp.rows.push_back(c.mod->sqr(sp.rows.back()));
+    out.assign(sp.rows.begin(), sp.rows.begin() + levels);
+}
+}  // namespace
+
+int vmt_stream_generate(int variant, uint64_t seed, uint64_t jump, int64_t n, int dtype, void* out_dev,
+                        void* cuda_stream)
+{
+    if (!valid_variant(variant)) return fail(VMT_EINVAL, "bad variant");
+    const bool type_ok = variant == VMT_MT19937_64 ? (dtype == VMT_U64 || dtype == VMT_F64 || dtype == VMT_F32)
+                                                   : (dtype == VMT_U32 || dtype == VMT_F32);
+    if (!type_ok) return fail(VMT_EINVAL, "output type must take one word of the generator");
+    if (n < 0 || n > (int64_t(1) << 39)) return fail(VMT_EINVAL, "n must be in 0 .. 2^39");
+    if (n > 0 && !out_dev) return fail(VMT_EINVAL, "null output");
+    if (n == 0) return VMT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int64_t B = vmt::block_words(variant, 1);
+    const int64_t blocks = (n + B - 1) / B;
+    // up to 2048 chunks (one warp or a few threads each), at least 64 blocks long
+    const int64_t chunk_blocks = std::max<int64_t>(64, (blocks + 2047) / 2048);
+    const int64_t P = (blocks + chunk_blocks - 1) / chunk_blocks;   // <= 2048
+    const int64_t chunk_words = chunk_blocks * B;
+    int levels = 0;
+    while ((int64_t(1) << levels) < P) ++levels;
+    const int64_t gen_bytes = vmt::state_bytes_per_gen(variant, 1);
+
+    // chunk 0: the base generator advanced by `jump` (seeding as vmt_init)
+    vmt_state* st0 = nullptr;
+    int rc = vmt::init_batch_impl(&st0, variant, 1, 1, &seed, &jump, s, true);
+    if (rc) return rc;
+    vmt_state* cs = nullptr;
+    rc = vmt::alloc_states_async(&cs, variant, 1, P, s);
+    if (rc) {
+        vmt::free_state_async(st0, s);
+        return rc;
+    }
+    uint32_t* d_rows = nullptr;
+    vmt::JumpItem* d_items = nullptr;
+    vmt::UnitDesc* d_units = nullptr;
+    int* d_counter = nullptr;
+    rc = [&]() -> int {
+        CUDA_TRY(cudaMemcpyAsync(cs->d_states, st0->d_states, static_cast<size_t>(gen_bytes), cudaMemcpyDeviceToDevice,
+                                 s));
+        if (P > 1) {
+            std::vector<Poly> polys;
+            stream_polys(variant, static_cast<uint64_t>(chunk_blocks) * vmt::units_per_lane(variant), levels, polys);
+            std::vector<uint32_t> rows(static_cast<size_t>(levels) * vmt::kPolyWords, 0);
+            std::vector<int> deg(static_cast<size_t>(levels));
+            for (int k = 0; k < levels; ++k) {
+                to_rows(polys[static_cast<size_t>(k)], &rows[static_cast<size_t>(k) * vmt::kPolyWords]);
+                deg[static_cast<size_t>(k)] = vmt::gf2::degree(polys[static_cast<size_t>(k)]);
+            }
+            CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_rows), rows.size() * 4, s));
+            CUDA_TRY(cudaMemcpyAsync(d_rows, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, s));
+            // level k: chunks [2^k, min(2^(k+1), P)) from chunks 2^k earlier
+            std::vector<vmt::JumpItem> items;
+            std::vector<std::pair<int64_t, int64_t>> level_range;
+            char* base = static_cast<char*>(cs->d_states);
+            for (int k = 0; k < levels; ++k) {
+                const int64_t lo = int64_t(1) << k, hi = std::min<int64_t>(int64_t(2) << k, P);
+                level_range.push_back({static_cast<int64_t>(items.size()), hi - lo});
+                for (int64_t j = lo; j < hi; ++j) {
+                    vmt::JumpItem it{};
+                    it.src = base + (j - lo) * gen_bytes;
+                    it.dst = base + j * gen_bytes;
+                    it.src_stride = 1;
+                    it.dst_stride = 1;
+                    it.poly = k;
+                    it.deg = deg[static_cast<size_t>(k)];
+                    items.push_back(it);
+                }
+            }
+            CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_items), items.size() * sizeof(vmt::JumpItem), s));
+            CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(vmt::JumpItem),
+                                     cudaMemcpyHostToDevice, s));
+            for (const auto& lr : level_range)
+                CUDA_TRY(vmt::launch_jump(variant, d_items + lr.first, static_cast<long long>(lr.second), d_rows, s));
+        }
+        // one unit per chunk; the last one takes the rest
+        std::vector<vmt::UnitDesc> units(static_cast<size_t>(P));
+        const int64_t eb = elem_bytes(dtype);
+        for (int64_t j = 0; j < P; ++j) {
+            vmt::UnitDesc& u = units[static_cast<size_t>(j)];
+            u.state = static_cast<char*>(cs->d_states) + j * gen_bytes;
+            u.pos = cs->d_pos + j;
+            u.total = std::min<int64_t>(chunk_words, n - j * chunk_words);
+            u.out = static_cast<char*>(out_dev) + j * chunk_words * eb;
+        }
+        CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_units), units.size() * sizeof(vmt::UnitDesc), s));
+        CUDA_TRY(cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(vmt::UnitDesc), cudaMemcpyHostToDevice,
+                                 s));
+        CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_counter), sizeof(int), s));
+        return vmt::launch_unit_table(variant, 1, dtype, d_units, P, d_counter, s);
+    }();
+    if (d_rows) cudaFreeAsync(d_rows, s);
+    if (d_items) cudaFreeAsync(d_items, s);
+    if (d_units) cudaFreeAsync(d_units, s);
+    if (d_counter) cudaFreeAsync(d_counter, s);
+    vmt::free_state_async(st0, s);
+    vmt::free_state_async(cs, s);
+    return rc;
+}
+
 int vmt_tune_jump_set(int variant, int64_t split_below)
 {
     if (split_below < 0) return fail(VMT_EINVAL, "split_below must be >= 0");

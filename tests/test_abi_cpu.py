@@ -51,6 +51,8 @@ def test_invalid_arguments_rejected(L):
     assert L.vmt_state_import(None, None, 0, None) == vmt.VMT_EINVAL
     assert L.vmt_prepare(3, None) == vmt.VMT_EINVAL
     assert L.vmt_measure_store_bw(1024, 1, None, None) == vmt.VMT_EINVAL
+    assert L.vmt_stream_generate(1, 1, 0, 10, vmt.DTYPES["u32"], None, None) == vmt.VMT_EINVAL   # u32 from MT64
+    assert L.vmt_stream_generate(0, 1, 0, 10, vmt.DTYPES["u32"], None, None) == vmt.VMT_EINVAL   # null output
     assert L.vmt_tune_jump_set(5, 10) == vmt.VMT_EINVAL
 
 
