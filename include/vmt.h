@@ -219,6 +219,7 @@ typedef struct {
     int64_t queued, in_flight_batches, batches, completed, failed, bytes_out;
     int64_t state_bytes_in_use, output_bytes_in_use, peak_state_bytes, peak_output_bytes;
     double host_launch_s, init_gpu_s, batch_gpu_s;
+    int64_t cancelled;
 } vmt_server_counters;
 
 int vmt_server_create(vmt_server** s, const vmt_server_config* cfg);
@@ -226,6 +227,21 @@ int vmt_server_submit(vmt_server* s, const vmt_request* r, uint64_t* id);
 int vmt_server_poll(vmt_server* s, uint64_t id, int* status, void** out_dev, int64_t* bytes, double* latency_s);
 int vmt_server_wait(vmt_server* s, uint64_t id, int timeout_ms);
 int vmt_server_release(vmt_server* s, uint64_t id);
+/*
+ * vmt_server_cancel -- withdraw a request that is still queued: its status
+ * becomes VMT_ECANCELED (release it as any finished request).  VMT_EBUSY when
+ * it is already running or finished, VMT_EINVAL for an unknown id.
+ */
+#define VMT_ECANCELED (-7)
+int vmt_server_cancel(vmt_server* s, uint64_t id);
+/*
+ * vmt_server_inject -- host-side fault injection for tests: the next `count`
+ * output allocations of the server fail as if device memory were exhausted
+ * (VMT_INJECT_ALLOC).  Each such request fails alone with VMT_ENOMEM; the
+ * rest of its batch and the server go on.  No GPU fault is involved.
+ */
+#define VMT_INJECT_ALLOC 1
+int vmt_server_inject(vmt_server* s, int what, int count);
 /* copy a finished request's output into host memory (cap bytes; synchronous) */
 int vmt_server_copy(vmt_server* s, uint64_t id, void* host_buf, int64_t cap);
 int vmt_server_stats(vmt_server* s, vmt_server_counters* stats);
@@ -320,6 +336,17 @@ int vmt_stream_generate(int variant, uint64_t seed, uint64_t jump, int64_t n, in
  * the buffer cannot be allocated.
  */
 int vmt_measure_store_bw(int64_t bytes, int reps, double* best_gbs, void* cuda_stream);
+
+/*
+ * vmt_selftest_wait -- diagnostic, no paper counterpart: runs the bounded
+ * mbarrier wait of the generation kernels on a barrier that nothing arrives
+ * at, with a limit of limit_ns (1 us .. 10 s), on the device's legacy stream.
+ * Returns VMT_ETIMEOUT when the wait gave up (the expected outcome; the
+ * kernel then returns normally and the context stays usable), VMT_OK if it
+ * did not, with the device-measured wait time in *elapsed_ns (may be null).
+ * The generation kernels use a limit of one second per wait.
+ */
+int vmt_selftest_wait(int64_t limit_ns, int64_t* elapsed_ns);
 int vmt_autotune(int variant, int lanes, int64_t count, int64_t n_per_gen, int dtype, int reps, void* cuda_stream,
                  int* best_threads, double* best_ms);
 

@@ -27,6 +27,8 @@ DTYPES = {"u32": 0, "u64": 1, "f32": 2, "f64": 3}
 UNITS = {0: 624, 1: 312, 2: 156}
 
 VMT_OK, VMT_EINVAL, VMT_ENOMEM, VMT_ECUDA, VMT_ETIMEOUT, VMT_EBUSY, VMT_ESTATE = 0, -1, -2, -3, -4, -5, -6
+VMT_ECANCELED = -7
+VMT_INJECT_ALLOC = 1
 
 _lib = None
 _lock = threading.Lock()
@@ -84,6 +86,9 @@ def lib() -> ctypes.CDLL:
             "vmt_server_release": (I, [P, U64]),
             "vmt_server_copy": (I, [P, U64, P, I64]),
             "vmt_server_stats": (I, [P, P]),
+            "vmt_server_cancel": (I, [P, U64]),
+            "vmt_server_inject": (I, [P, I, I]),
+            "vmt_selftest_wait": (I, [I64, P]),
             "vmt_server_destroy": (None, [P]),
             "vmt_tune_set": (I, [I, I, I]),
             "vmt_tune_get": (I, [I, I]),
@@ -277,7 +282,7 @@ class _Counters(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("queued", "in_flight_batches", "batches", "completed", "failed",
                                              "bytes_out", "state_bytes_in_use", "output_bytes_in_use",
                                              "peak_state_bytes", "peak_output_bytes")] + \
-        [(n, ctypes.c_double) for n in ("host_launch_s", "init_gpu_s", "batch_gpu_s")]
+        [(n, ctypes.c_double) for n in ("host_launch_s", "init_gpu_s", "batch_gpu_s")] + [("cancelled", ctypes.c_int64)]
 
 
 class Server:
@@ -316,6 +321,14 @@ class Server:
 
     def release(self, rid: int) -> None:
         _check(lib().vmt_server_release(self._h, rid))
+
+    def cancel(self, rid: int) -> None:
+        """Withdraw a queued request (its status becomes VMT_ECANCELED)."""
+        _check(lib().vmt_server_cancel(self._h, rid))
+
+    def inject_alloc_failures(self, count: int) -> None:
+        """Fault injection: the next `count` output allocations fail."""
+        _check(lib().vmt_server_inject(self._h, VMT_INJECT_ALLOC, int(count)))
 
     def stats(self) -> dict:
         c = _Counters()
@@ -375,6 +388,16 @@ def stream_generate(variant: str, seed: int, n: int, dtype: str = "u32", jump: i
     _check(lib().vmt_stream_generate(VARIANTS[variant], int(seed) & (2**64 - 1), int(jump) & (2**64 - 1), int(n),
                                      DTYPES[dtype], ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
     return out
+
+
+def selftest_wait(limit_ns: int = 1_000_000) -> tuple[int, int]:
+    """Run a bounded device wait that nothing satisfies; returns (status,
+    elapsed ns) -- status VMT_ETIMEOUT when the wait gave up as designed."""
+    el = ctypes.c_int64(0)
+    rc = lib().vmt_selftest_wait(int(limit_ns), ctypes.byref(el))
+    if rc not in (VMT_OK, VMT_ETIMEOUT):
+        _check(rc)
+    return rc, el.value
 
 
 def measure_store_bw(nbytes: int = 8 << 30, reps: int = 5, stream=None) -> float:

@@ -1,14 +1,23 @@
 // bulk.cuh -- 1-D bulk copies between global and shared memory (the TMA's
 // cp.async.bulk, sm_90+) with mbarrier completion, for staging whole
-// generator states.  Every wait is bounded: after kMaxPolls polls it gives up
-// and reports a timeout instead of spinning forever.
+// generator states.  Every wait is bounded: after kWaitLimitNs of global time
+// (or kMaxPolls polls, whichever comes first) it gives up and reports a
+// timeout instead of spinning forever.
 #pragma once
 #include <cstdint>
 
 namespace vmt {
 namespace dev {
 
-constexpr unsigned kMaxPolls = 1u << 24;
+constexpr unsigned kMaxPolls = 1u << 26;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // one second
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
@@ -51,10 +60,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 }
 
 // bounded wait for the phase with the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns = kWaitLimitNs)
 {
-    for (unsigned i = 0; i < kMaxPolls; ++i)
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned i = 0; i < kMaxPolls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 63u && globaltimer_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 

@@ -69,6 +69,7 @@ struct Req {
     int64_t bytes = 0;
     int64_t state_bytes = 0;
     int64_t chunks = 1;      // generators it runs on (one per chunk)
+    int launch_rc = VMT_OK;  // set when its own launch step failed (it fails alone)
     bool admitted = false;   // its output bytes count against the budget
     double t_submit = 0, t_done = 0;
 };
@@ -117,6 +118,8 @@ struct vmt_server {
     int64_t used_state = 0, used_out = 0, peak_state = 0, peak_out = 0;
     int64_t batches = 0, completed = 0, failed = 0, bytes_out = 0;
     double host_launch_s = 0, init_gpu_s = 0, batch_gpu_s = 0;
+    int64_t cancelled = 0;
+    std::atomic<int> inject_alloc{0};   // output allocations still to fail (fault injection)
     cudaMemPool_t pool = nullptr;   // states and outputs
     // Memory is freed on a stream of its own, only ever after the kernels that
     // used it have finished, so reuse of a freed block never waits for other work.
@@ -196,13 +199,21 @@ int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
             const int wpo = words_per_out(variant, dtype);
             for (int64_t i = 0; i < k; ++i) {
                 Req* q = rq[idx[static_cast<size_t>(i)]];
-                if (cudaMallocFromPoolAsync(&q->out, static_cast<size_t>(std::max<int64_t>(q->bytes, 16)), s->pool,
-                                            s_init) != cudaSuccess)
-                    return VMT_ENOMEM;
+                // an injected failure stands for a failed allocation call
+                int inj = s->inject_alloc.load();
+                while (inj > 0 && !s->inject_alloc.compare_exchange_weak(inj, inj - 1)) {
+                }
+                if (inj > 0 || cudaMallocFromPoolAsync(&q->out, static_cast<size_t>(std::max<int64_t>(q->bytes, 16)),
+                                                       s->pool, s_init) != cudaSuccess) {
+                    if (inj <= 0) cudaGetLastError();
+                    q->out = nullptr;
+                    q->launch_rc = VMT_ENOMEM;   // this request fails alone
+                }
             }
             // chunks: request i, chunk c in 1..P_i-1
             int64_t nchunk = 0;
             for (int64_t i = 0; i < k; ++i) {
+                if (!rq[idx[static_cast<size_t>(i)]]->out) continue;
                 const int64_t P = n_chunks(variant, lanes, rq[idx[static_cast<size_t>(i)]]->r.n * wpo);
                 for (int64_t c = 1; c < P; ++c)
                     sl.h_map[map0 + nchunk++] = make_int2(static_cast<int>(i), static_cast<int>(c));
@@ -240,7 +251,7 @@ int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
             for (int64_t i = 0; i < k; ++i) {
                 Req* q = rq[idx[static_cast<size_t>(i)]];
                 const int64_t w = q->r.n * wpo;
-                if (w == 0) continue;
+                if (w == 0 || !q->out) continue;
                 const int64_t P = n_chunks(variant, lanes, w);
                 for (int64_t c = 0; c < P; ++c) {
                     vmt::UnitDesc u{};
@@ -293,8 +304,9 @@ std::vector<std::pair<vmt_state*, cudaStream_t>> retire(vmt_server* s, std::vect
         for (uint64_t id : b->ids) {
             auto it = s->reqs.find(id);
             if (it == s->reqs.end()) continue;
-            if (it->second.status == VMT_SERVER_RUNNING && b->rc) {
-                it->second.status = b->rc;   // reported only now: its batch's kernels have finished
+            if (it->second.status == VMT_SERVER_RUNNING && (b->rc || it->second.launch_rc)) {
+                // reported only now: its batch's kernels have finished
+                it->second.status = b->rc ? b->rc : it->second.launch_rc;
                 ++s->failed;
             } else if (it->second.status == VMT_SERVER_RUNNING) {
                 it->second.status = VMT_SERVER_DONE;
@@ -593,6 +605,37 @@ int vmt_server_release(vmt_server* s, uint64_t id)
     return VMT_OK;
 }
 
+int vmt_server_cancel(vmt_server* s, uint64_t id)
+{
+    if (!s) return VMT_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) {
+        vmt::set_last_error("vmt_server_cancel: unknown request id");
+        return VMT_EINVAL;
+    }
+    if (it->second.status != VMT_SERVER_QUEUED) {
+        vmt::set_last_error("vmt_server_cancel: request already running or finished");
+        return VMT_EBUSY;
+    }
+    auto q = std::find(s->queue.begin(), s->queue.end(), id);
+    if (q != s->queue.end()) s->queue.erase(q);
+    it->second.status = VMT_ECANCELED;
+    ++s->cancelled;
+    s->cv_done.notify_all();
+    return VMT_OK;
+}
+
+int vmt_server_inject(vmt_server* s, int what, int count)
+{
+    if (!s || what != VMT_INJECT_ALLOC || count < 0) {
+        vmt::set_last_error("vmt_server_inject: unknown fault or negative count");
+        return VMT_EINVAL;
+    }
+    s->inject_alloc.store(count);
+    return VMT_OK;
+}
+
 int vmt_server_stats(vmt_server* s, vmt_server_counters* out)
 {
     if (!s || !out) return VMT_EINVAL;
@@ -610,6 +653,7 @@ int vmt_server_stats(vmt_server* s, vmt_server_counters* out)
     out->host_launch_s = s->host_launch_s;
     out->init_gpu_s = s->init_gpu_s;
     out->batch_gpu_s = s->batch_gpu_s;
+    out->cancelled = s->cancelled;
     return VMT_OK;
 }
 

@@ -54,6 +54,9 @@ def test_invalid_arguments_rejected(L):
     assert L.vmt_stream_generate(1, 1, 0, 10, vmt.DTYPES["u32"], None, None) == vmt.VMT_EINVAL   # u32 from MT64
     assert L.vmt_stream_generate(0, 1, 0, 10, vmt.DTYPES["u32"], None, None) == vmt.VMT_EINVAL   # null output
     assert L.vmt_tune_jump_set(5, 10) == vmt.VMT_EINVAL
+    assert L.vmt_selftest_wait(10, None) == vmt.VMT_EINVAL
+    assert L.vmt_server_cancel(None, 1) == vmt.VMT_EINVAL
+    assert L.vmt_server_inject(None, vmt.VMT_INJECT_ALLOC, 1) == vmt.VMT_EINVAL
 
 
 @pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])

@@ -167,3 +167,61 @@ def test_reserved_pool_and_counters(vmt):
     with pytest.raises(vmt.VMTError) as ei:   # budgets larger than the device: creation fails cleanly
         vmt.Server(state_budget=1 << 30, output_budget=4 * free, max_batch=8, reserve=True)
     assert ei.value.code == vmt.VMT_ENOMEM
+
+
+def test_cancel_queued_request(vmt):
+    # a small output budget keeps the later requests queued behind the first
+    srv = vmt.Server(state_budget=1 << 30, output_budget=(4 << 20) + 64, max_batch=16)
+    a = srv.submit("mt32", 4, "u32", 1, 0, 1 << 20)     # 4 MiB: the whole budget
+    b = srv.submit("mt32", 4, "u32", 2, 0, 1000)
+    c = srv.submit("mt32", 4, "u32", 3, 0, 1000)
+    srv.wait(a)
+    assert srv.poll(c)[0] == vmt.SERVER_QUEUED            # a is not released yet
+    srv.cancel(c)
+    with pytest.raises(vmt.VMTError) as ei:
+        srv.wait(c)
+    assert ei.value.code == vmt.VMT_ECANCELED
+    with pytest.raises(vmt.VMTError) as ei:
+        srv.cancel(a)                                     # finished: cannot be withdrawn
+    assert ei.value.code == vmt.VMT_EBUSY
+    srv.release(a)
+    srv.wait(b)
+    assert np.array_equal(srv.copy(b, "u32"), _alone(vmt, "mt32", 4, "u32", 2, 0, 1000))
+    srv.release(b)
+    srv.release(c)
+    st = srv.stats()
+    assert st["cancelled"] == 1 and st["completed"] == 2
+    srv.close()
+
+
+def test_injected_allocation_failures_fail_alone(vmt):
+    srv = vmt.Server(state_budget=1 << 30, output_budget=1 << 30, max_batch=64)
+    srv.inject_alloc_failures(2)
+    cases = [("mt32", 4, "u32", 50 + i, i, 20000 + 7 * i) for i in range(6)]
+    ids = [srv.submit(*c) for c in cases]
+    failed = 0
+    for rid, c in zip(ids, cases):
+        try:
+            srv.wait(rid)
+        except vmt.VMTError as e:
+            assert e.code == vmt.VMT_ENOMEM
+            failed += 1
+        else:
+            assert np.array_equal(srv.copy(rid, "u32"), _alone(vmt, *c))
+        srv.release(rid)
+    assert failed == 2
+    rid = srv.submit("mt32", 4, "u32", 99, 0, 5000)      # the server goes on
+    srv.wait(rid)
+    srv.release(rid)
+    srv.close()
+
+
+def test_device_wait_gives_up_with_status(vmt):
+    # a bounded wait on a barrier nothing arrives at ends with a status, and
+    # the context stays usable (no trap, no hang)
+    rc, elapsed = vmt.selftest_wait(2_000_000)            # 2 ms limit
+    assert rc == vmt.VMT_ETIMEOUT
+    assert 2_000_000 <= elapsed < 1_000_000_000
+    assert vmt.device_status() == 0                       # generation kernels untouched
+    g = vmt.VGenerator("mt32", 4, [1])
+    assert g.generate(100, "u32").numel() == 100
