@@ -496,6 +496,21 @@ def run_gb300(args, world, rank, local):
                                            "generation"}
         del sbuf
 
+    # buffered scalar queries on the host: one 16-lane MT32 generator, single
+    # queries served from pinned buffers refilled in bulk by the GPU
+    scalar = None
+    if not args.no_scalar:
+        sq = vmt.ScalarGenerator("mt32", 16, 5489, 0, "u32", buffer_outputs=1 << 22)
+        sq.drain(1 << 24)                   # warm-up
+        nq = 1 << 28
+        t0 = time.perf_counter()
+        sq.drain(nq)
+        sq_s = time.perf_counter() - t0
+        sq.close()
+        scalar = {"value": nq / sq_s, "unit": "queries/s", "queries": nq, "seconds": sq_s,
+                  "note": "vmt_scalar_drain: one u32 per query from a 16-lane MT32 V-generator, buffers of 2^22 "
+                          "outputs refilled by the GPU while the host reads the other one"}
+
     served = None
     if not args.no_serve:
         served = run_served(vmt, args.serve_requests, 2.0e4, args.plain_requests)
@@ -544,6 +559,7 @@ def run_gb300(args, world, rank, local):
                              "variant's polynomial tables prepared first, untimed)"},
             "jump": jump,
             "single_stream": single,
+            "scalar_queries": scalar,
             "clocks": clocks,
             "served": served,
         }
@@ -562,6 +578,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the served-mix measurement")
     ap.add_argument("--no-jump", action="store_true", help="skip the full-size jump measurement")
     ap.add_argument("--no-stream", action="store_true", help="skip the single-stream measurement")
+    ap.add_argument("--no-scalar", action="store_true", help="skip the scalar-query measurement")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--plain-requests", type=int, default=1000)
     ap.add_argument("--generators", type=int, default=0,

@@ -327,6 +327,31 @@ int vmt_stream_generate(int variant, uint64_t seed, uint64_t jump, int64_t n, in
                         void* cuda_stream);
 
 /*
+ * Buffered scalar queries (the paper's scalar query mode, served from a
+ * buffer; Sec. 5, scalar performance and optimised buffering).  One
+ * V-generator (variant, lanes, seed, jump as in vmt_init) whose outputs of
+ * type dtype are read one at a time on the host: they are produced by the GPU
+ * in bulk, buffer_outputs (1024 .. 2^28) at a time, into one of two pinned
+ * host buffers while the host reads the other.  The sequence is exactly the
+ * V-stream S that vmt_generate would return for the same generator.
+ *   vmt_scalar_next   the next output (4 or 8 bytes) into *value
+ *   vmt_scalar_take   the next n outputs into host memory
+ *   vmt_scalar_drain  consumes `count` outputs one query at a time and returns
+ *                     an order-sensitive checksum of them (measures the
+ *                     per-query cost without a caller's loop)
+ * Not thread-safe: one object per consuming thread.  Calls wait for a refill
+ * only once every buffer_outputs outputs.  Errors: VMT_EINVAL, VMT_ENOMEM,
+ * VMT_ECUDA; the restrictions of vmt_generate on dtype apply.
+ */
+typedef struct vmt_scalar vmt_scalar;
+int vmt_scalar_create(vmt_scalar** q, int variant, int lanes, uint64_t seed, uint64_t jump, int dtype,
+                      int64_t buffer_outputs);
+int vmt_scalar_next(vmt_scalar* q, void* value);
+int vmt_scalar_take(vmt_scalar* q, int64_t n, void* out_host);
+int vmt_scalar_drain(vmt_scalar* q, int64_t count, uint64_t* checksum);
+void vmt_scalar_destroy(vmt_scalar* q);
+
+/*
  * vmt_measure_store_bw -- diagnostic, no paper counterpart: the device's HBM
  * write bandwidth as seen by a store-only kernel (16-byte streaming stores
  * over `bytes` bytes of a buffer it allocates and frees on cuda_stream), best

@@ -89,6 +89,11 @@ def lib() -> ctypes.CDLL:
             "vmt_server_cancel": (I, [P, U64]),
             "vmt_server_inject": (I, [P, I, I]),
             "vmt_selftest_wait": (I, [I64, P]),
+            "vmt_scalar_create": (I, [PP, I, I, U64, U64, I, I64]),
+            "vmt_scalar_next": (I, [P, P]),
+            "vmt_scalar_take": (I, [P, I64, P]),
+            "vmt_scalar_drain": (I, [P, I64, P]),
+            "vmt_scalar_destroy": (None, [P]),
             "vmt_server_destroy": (None, [P]),
             "vmt_tune_set": (I, [I, I, I]),
             "vmt_tune_get": (I, [I, I]),
@@ -388,6 +393,46 @@ def stream_generate(variant: str, seed: int, n: int, dtype: str = "u32", jump: i
     _check(lib().vmt_stream_generate(VARIANTS[variant], int(seed) & (2**64 - 1), int(jump) & (2**64 - 1), int(n),
                                      DTYPES[dtype], ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
     return out
+
+
+class ScalarGenerator:
+    """Buffered scalar queries on the host from one V-generator
+    (vmt_scalar_*): next() returns one output, take(n) the next n."""
+
+    def __init__(self, variant: str, lanes: int, seed: int, jump: int = 0, dtype: str = "u32",
+                 buffer_outputs: int = 1 << 20):
+        h = ctypes.c_void_p()
+        _check(lib().vmt_scalar_create(ctypes.byref(h), VARIANTS[variant], int(lanes), int(seed) & (2**64 - 1),
+                                       int(jump) & (2**64 - 1), DTYPES[dtype], int(buffer_outputs)))
+        self._h = h
+        self.dtype = dtype
+        self._np = {"u32": np.uint32, "u64": np.uint64, "f32": np.float32, "f64": np.float64}[dtype]
+
+    def next(self):
+        v = np.zeros(1, self._np)
+        _check(lib().vmt_scalar_next(self._h, _np_ptr(v)))
+        return v[0]
+
+    def take(self, n: int) -> np.ndarray:
+        out = np.empty(int(n), self._np)
+        _check(lib().vmt_scalar_take(self._h, int(n), _np_ptr(out)))
+        return out
+
+    def drain(self, count: int) -> int:
+        c = ctypes.c_uint64(0)
+        _check(lib().vmt_scalar_drain(self._h, int(count), ctypes.byref(c)))
+        return c.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vmt_scalar_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def selftest_wait(limit_ns: int = 1_000_000) -> tuple[int, int]:
