@@ -233,6 +233,14 @@ int vmt_server_release(vmt_server* s, uint64_t id);
  * it is already running or finished, VMT_EINVAL for an unknown id.
  */
 #define VMT_ECANCELED (-7)
+/*
+ * vmt_server_next_done -- completion queue: the id of the next request that
+ * reached a final status (done, failed or cancelled), in the order they did,
+ * each once; waits up to timeout_us microseconds and returns VMT_ETIMEOUT if
+ * none came.  Requests released before they were taken from the queue are
+ * skipped.
+ */
+int vmt_server_next_done(vmt_server* s, int64_t timeout_us, uint64_t* id);
 int vmt_server_cancel(vmt_server* s, uint64_t id);
 /*
  * vmt_server_inject -- host-side fault injection for tests: the next `count`

@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
             "vmt_server_copy": (I, [P, U64, P, I64]),
             "vmt_server_stats": (I, [P, P]),
             "vmt_server_cancel": (I, [P, U64]),
+            "vmt_server_next_done": (I, [P, I64, P]),
             "vmt_server_inject": (I, [P, I, I]),
             "vmt_selftest_wait": (I, [I64, P]),
             "vmt_scalar_create": (I, [PP, I, I, U64, U64, I, I64]),
@@ -326,6 +327,16 @@ class Server:
 
     def release(self, rid: int) -> None:
         _check(lib().vmt_server_release(self._h, rid))
+
+    def next_done(self, timeout_us: int = 0):
+        """Id of the next request that finished (in completion order), or None
+        if none finished within timeout_us."""
+        rid = ctypes.c_uint64(0)
+        rc = lib().vmt_server_next_done(self._h, int(timeout_us), ctypes.byref(rid))
+        if rc == VMT_ETIMEOUT:
+            return None
+        _check(rc)
+        return rid.value
 
     def cancel(self, rid: int) -> None:
         """Withdraw a queued request (its status becomes VMT_ECANCELED)."""

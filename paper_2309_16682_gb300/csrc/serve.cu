@@ -112,6 +112,7 @@ struct vmt_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
+    std::deque<uint64_t> done_q;   // requests that reached a final status, in that order
     std::unordered_map<uint64_t, Req> reqs;
     std::deque<Batch*> inflight;
     Slot slots[kSlots];
@@ -241,7 +242,6 @@ int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
             const auto& idx = kv.second;
             const int64_t k = static_cast<int64_t>(idx.size());
             const int wpo = words_per_out(variant, dtype);
-            const int64_t C = vmt::chunk_words(variant, lanes);
             const int64_t gen_bytes = vmt::state_bytes_per_gen(variant, lanes);
             const int eb = out_bytes(dtype);
             const vmt_state* st = sts[static_cast<size_t>(gi)];
@@ -252,6 +252,7 @@ int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
                 Req* q = rq[idx[static_cast<size_t>(i)]];
                 const int64_t w = q->r.n * wpo;
                 if (w == 0 || !q->out) continue;
+                const int64_t C = vmt::chunk_words(variant, lanes);
                 const int64_t P = n_chunks(variant, lanes, w);
                 for (int64_t c = 0; c < P; ++c) {
                     vmt::UnitDesc u{};
@@ -308,11 +309,13 @@ std::vector<std::pair<vmt_state*, cudaStream_t>> retire(vmt_server* s, std::vect
                 // reported only now: its batch's kernels have finished
                 it->second.status = b->rc ? b->rc : it->second.launch_rc;
                 ++s->failed;
+                s->done_q.push_back(id);
             } else if (it->second.status == VMT_SERVER_RUNNING) {
                 it->second.status = VMT_SERVER_DONE;
                 it->second.t_done = b->t_done;
                 ++s->completed;
                 s->bytes_out += it->second.bytes;
+                s->done_q.push_back(id);
             }
         }
         slots.push_back(b->slot);   // its events are read before the slot is reused
@@ -361,6 +364,7 @@ void worker_main(vmt_server* s)
             if (q.state_bytes > s->cfg.state_budget_bytes || q.bytes > s->cfg.output_budget_bytes) {
                 q.status = VMT_ENOMEM;   // can never be admitted
                 ++s->failed;
+                s->done_q.push_back(id);
                 s->queue.pop_front();
                 s->cv_done.notify_all();
                 continue;
@@ -605,6 +609,21 @@ int vmt_server_release(vmt_server* s, uint64_t id)
     return VMT_OK;
 }
 
+int vmt_server_next_done(vmt_server* s, int64_t timeout_us, uint64_t* id)
+{
+    if (!s || !id || timeout_us < 0) return VMT_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    // ids of released requests are skipped (their owner has seen them already)
+    auto ready = [&] {
+        while (!s->done_q.empty() && !s->reqs.count(s->done_q.front())) s->done_q.pop_front();
+        return !s->done_q.empty();
+    };
+    if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) return VMT_ETIMEOUT;
+    *id = s->done_q.front();
+    s->done_q.pop_front();
+    return VMT_OK;
+}
+
 int vmt_server_cancel(vmt_server* s, uint64_t id)
 {
     if (!s) return VMT_EINVAL;
@@ -622,6 +641,7 @@ int vmt_server_cancel(vmt_server* s, uint64_t id)
     if (q != s->queue.end()) s->queue.erase(q);
     it->second.status = VMT_ECANCELED;
     ++s->cancelled;
+    s->done_q.push_back(id);
     s->cv_done.notify_all();
     return VMT_OK;
 }

@@ -225,3 +225,35 @@ def test_device_wait_gives_up_with_status(vmt):
     assert vmt.device_status() == 0                       # generation kernels untouched
     g = vmt.VGenerator("mt32", 4, [1])
     assert g.generate(100, "u32").numel() == 100
+
+
+def test_completion_queue_reports_each_request_once(vmt):
+    srv = vmt.Server(state_budget=1 << 30, output_budget=1 << 30, max_batch=8)
+    assert srv.next_done(1000) is None                    # nothing submitted yet
+    sizes = [50_000, 10, 3_000_000, 777, 120_000, 1, 64_000, 5]
+    ids = [srv.submit("mt64", 4, "u64", 10 + i, 0, n) for i, n in enumerate(sizes)]
+    bad = srv.submit("mt32", 4, "u32", 1, 0, 300_000_000)  # 1.2 GB > budget: fails at admission
+    seen = []
+    while len(seen) < len(ids) + 1:
+        rid = srv.next_done(5_000_000)
+        assert rid is not None
+        seen.append(rid)
+        st = srv.poll(rid)[0]
+        assert st == vmt.SERVER_DONE or (rid == bad and st == vmt.VMT_ENOMEM)
+        srv.release(rid)
+    assert sorted(seen) == sorted(ids + [bad])
+    assert srv.next_done(1000) is None
+    srv.close()
+
+
+def test_large_batch_uses_longer_chunks_and_stays_exact(vmt):
+    # one batch writing several GB: chunks span several table steps (c * m)
+    srv = vmt.Server(state_budget=1 << 30, output_budget=12 << 30, max_batch=64)
+    cases = [("mt32", 2, "u32", 70 + i, i, 250_000_000 + 1237 * i) for i in range(8)]   # 1 GB each
+    ids = [srv.submit(*c) for c in cases]
+    for k, (rid, c) in enumerate(zip(ids, cases)):
+        srv.wait(rid)
+        if k in (0, 5):                                    # full comparison for two of them
+            assert np.array_equal(srv.copy(rid, "u32"), _alone(vmt, *c)), c
+        srv.release(rid)
+    srv.close()
