@@ -332,3 +332,23 @@ def test_two_shards_equal_one_run(vmt):
     whole = _np(vmt.VGenerator("mt32", 16, seeds).generate(5000, "u32"))
     parts = [_np(vmt.VGenerator("mt32", 16, shard.rank_seeds(name, 2, r, per)).generate(5000, "u32")) for r in range(2)]
     assert np.array_equal(np.concatenate(parts), whole)
+
+
+@pytest.mark.parametrize("variant,M,dtype", [(O.MT32, 16, "u32"), (O.MT64, 8, "f64"), (O.SFMT, 4, "u32")])
+def test_call_longer_than_one_launch_piece(vmt, oracle_polys, variant, M, dtype):
+    """One generator asked for more than 2^31 words in one call (the call is
+    cut into launches of at most 2^30 words): words around every cut and at
+    the end equal the oracle, whose lanes are jumped forward by whole blocks."""
+    wpo = O.words_per_output(variant, dtype)
+    n = ((1 << 31) + 4099) // wpo
+    g = vmt.VGenerator(VNAME[variant], M, [2024])
+    out = g.generate(n, dtype)[0]
+    lanes0 = O.lane_states(variant, M, 2024)
+    row_words = O.WORDS_PER_UNIT[variant] * M                 # one recurrence step of every lane
+    for w_at in [(1 << 30) - 700, (1 << 31) - 700, n * wpo - 1500]:
+        row = w_at // row_words                               # steps each lane has taken by then
+        lanes = [O.jump_by(st, row) for st in lanes0]
+        L = 1500
+        ref = O.vstream(variant, M, 0, L // wpo, dtype, start_word=w_at - row * row_words, lanes=lanes)
+        got = _np(out[w_at // wpo: w_at // wpo + L // wpo])
+        _assert_same(got, ref, f"{VNAME[variant]} word {w_at}")
