@@ -202,7 +202,7 @@ template <>
 __device__ __forceinline__ void extend<JSFMT>(uint4* ring, int gen, int lane)
 {
     // 32 elements at a time: every lane the chain-free part of one element,
-    // then lane 0 the chain through all 32
+    // then four lanes the chain through all 32
     constexpr int RG = JSFMT::RING, NN = JSFMT::N, MMM = JSFMT::MM;
     static_assert(JSFMT::G % 32 == 0 && NN - MMM >= 32, "blocks of 32 elements");
     uint4* pre = ring + RG;
@@ -210,9 +210,26 @@ __device__ __forceinline__ void extend<JSFMT>(uint4* ring, int gen, int lane)
         const int q = s0 + lane;
         pre[lane] = sfmt_pre(ring[(q - NN) % RG], ring[(q - NN + MMM) % RG]);
         __syncwarp();
-        if (lane == 0) {
-            uint4 c = ring[(s0 - 2) % RG], d = ring[(s0 - 1) % RG];
-            sfmt_chain_run<RG>(pre, ring, s0 % RG, 32, c, d);
+        if (lane < 4) {
+            // lanes 0..3 run the chain, lane j owning sub-word j; the 128-bit
+            // right shift of w_{q-2} takes sub-word j+1 from the next lane,
+            // passed one step ahead of its use
+            const uint32_t* p32 = reinterpret_cast<const uint32_t*>(pre);
+            uint32_t* r32 = reinterpret_cast<uint32_t*>(ring);
+            uint32_t c = r32[4 * ((s0 - 2) % RG) + lane], d = r32[4 * ((s0 - 1) % RG) + lane];
+            uint32_t cn = __shfl_down_sync(0xFu, c, 1, 4);
+            if (lane == 3) cn = 0u;
+            int iq = s0 % RG;
+#pragma unroll 8
+            for (int u = 0; u < 32; ++u) {
+                const uint32_t w = p32[4 * u + lane] ^ __funnelshift_r(c, cn, 8) ^ (d << 18);
+                r32[4 * iq + lane] = w;
+                const uint32_t dn = __shfl_down_sync(0xFu, d, 1, 4);
+                iq = iq + 1 == RG ? 0 : iq + 1;
+                c = d;
+                cn = lane == 3 ? 0u : dn;
+                d = w;
+            }
         }
         __syncwarp();
     }
