@@ -256,10 +256,11 @@ int vmt_server_stats(vmt_server* s, vmt_server_counters* stats);
 void vmt_server_destroy(vmt_server* s);
 
 /*
- * vmt_generate_host -- as vmt_generate but into host memory (pinned or
- * pageable): the words are generated into a device staging buffer in chunks
- * and copied to out_host, generation of one chunk overlapping the copy of the
- * previous one.  Synchronises `cuda_stream` before returning.
+ * vmt_generate_host -- as vmt_generate but into host memory.  Pinned
+ * (page-locked, device-mapped) memory is written directly by the generation
+ * kernels; pageable memory through a device staging buffer in chunks, the
+ * generation of one chunk overlapping the copy of the previous one.
+ * Synchronises `cuda_stream` before returning.
  */
 int vmt_generate_host(vmt_state* st, int64_t n, int dtype, void* out_host, void* cuda_stream);
 

@@ -1153,6 +1153,18 @@ int vmt_generate_host(vmt_state* st, int64_t n, int dtype, void* out_host, void*
     if (dtype < VMT_U32 || dtype > VMT_F64) return fail(VMT_EINVAL, "bad dtype");
     if (n == 0) return VMT_OK;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // Pinned host memory is mapped into the device's address space: the
+    // generation kernels store into it directly over the CPU-GPU link, with
+    // no staging buffer and no separate copy (on GB300 as fast as the copy
+    // engines, which share the same host-memory bandwidth).
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, out_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer != nullptr) {
+        int rc = vmt_generate(st, n, dtype, pa.devicePointer, cuda_stream);
+        if (rc == VMT_OK) CUDA_TRY(cudaStreamSynchronize(s));
+        return rc;
+    }
+    cudaGetLastError();
     const int64_t eb = elem_bytes(dtype);
     const int64_t row = n * eb;   // one generator's output bytes
     const int64_t kStage = int64_t(256) << 20;

@@ -178,13 +178,21 @@ def test_export_import_resume(vmt, oracle_polys):
         g2.import_state(bytes(bad))
 
 
-def test_generate_host_matches_device(vmt, oracle_polys):
+@pytest.mark.parametrize("memory", ["pinned", "pageable"])
+def test_generate_host_matches_device(vmt, oracle_polys, memory):
+    """Pinned buffers are written directly by the kernels, pageable ones
+    through staging; both equal the device path, over several calls."""
     seeds = I.splitmix64(5, 6)
     g1 = vmt.VGenerator("mt32", 16, seeds)
     g2 = vmt.VGenerator("mt32", 16, seeds)
-    d = _np(g1.generate(100003, "f32"))
-    h = g2.generate_host(100003, "f32").numpy()
-    assert np.array_equal(d, h)
+    for n, dt in [(100003, "f32"), (7, "u64"), (70001, "u32")]:
+        d = _np(g1.generate(n, dt))
+        if memory == "pinned":
+            h = g2.generate_host(n, dt).numpy()
+        else:
+            h = np.empty((6, n), dtype={"f32": np.float32, "u64": np.uint64, "u32": np.uint32}[dt])
+            g2.generate_host(n, dt, out=h)
+        assert np.array_equal(d, h), (memory, n, dt)
 
 
 def test_zero_and_empty_calls(vmt, oracle_polys):
