@@ -112,12 +112,6 @@ int fail(int code, const std::string& msg)
 
 bool valid_variant(int v) { return v == VMT_MT19937_32 || v == VMT_MT19937_64 || v == VMT_SFMT19937; }
 bool valid_lanes(int m) { return m == 1 || m == 2 || m == 4 || m == 8 || m == 16; }
-int log2i(int m)
-{
-    int l = 0;
-    while ((1 << l) < m) ++l;
-    return l;
-}
 
 // Lane spacing of Table "jvalues": J = 2^(19937 - log2 M).  Rows 0..15 of a
 // variant's device table hold x^(s * 2^19933) mod mu, s = 0..15, so lane t of
