@@ -339,9 +339,9 @@ int vmt_stream_generate(int variant, uint64_t seed, uint64_t jump, int64_t n, in
  * Buffered scalar queries (the paper's scalar query mode, served from a
  * buffer; Sec. 5, scalar performance and optimised buffering).  One
  * V-generator (variant, lanes, seed, jump as in vmt_init) whose outputs of
- * type dtype are read one at a time on the host: they are produced by the GPU
- * in bulk, buffer_outputs (1024 .. 2^28) at a time, into one of two pinned
- * host buffers while the host reads the other.  The sequence is exactly the
+ * type dtype are read one at a time on the host: the GPU's kernels write them
+ * in bulk, buffer_outputs (1024 .. 2^28) at a time, directly into one of two
+ * pinned, device-mapped host buffers while the host reads the other.  The sequence is exactly the
  * V-stream S that vmt_generate would return for the same generator.
  *   vmt_scalar_next   the next output (4 or 8 bytes) into *value
  *   vmt_scalar_take   the next n outputs into host memory

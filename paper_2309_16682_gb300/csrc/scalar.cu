@@ -4,10 +4,11 @@
 // Optimized Buffering").
 //
 // Here the bulk step is a GPU generation of K outputs of one V-generator
-// copied into pinned host memory.  Two host halves alternate: while the host
-// reads one, the GPU refills the other on the object's own stream, so a query
-// is a bounds check and a load except once every K queries, when it waits
-// for the refill that was started K queries earlier.
+// written straight into pinned host memory (mapped into the GPU's address
+// space).  Two host halves alternate: while the host reads one, the GPU
+// refills the other on the object's own stream, so a query is a bounds check
+// and a load except once every K queries, when it waits for the refill that
+// was started K queries earlier.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,7 +24,7 @@ struct vmt_scalar {
     int64_t K = 0;               // outputs per half
     cudaStream_t s = nullptr;
     unsigned char* host[2] = {nullptr, nullptr};   // pinned halves
-    void* dev[2] = {nullptr, nullptr};
+    void* mapped[2] = {nullptr, nullptr};          // the same halves as device addresses
     cudaEvent_t ready[2] = {nullptr, nullptr};
     int cur = 0;                 // half being read
     int64_t pos = 0;             // next output in it
@@ -31,14 +32,12 @@ struct vmt_scalar {
 
 namespace {
 
-// start refilling half h: generate K outputs on the device, copy them to the host
+// start refilling half h: the kernels write K outputs into it directly
 int refill(vmt_scalar* q, int h)
 {
-    int rc = vmt_generate(q->st, q->K, q->dtype, q->dev[h], q->s);
+    int rc = vmt_generate(q->st, q->K, q->dtype, q->mapped[h], q->s);
     if (rc) return rc;
-    if (cudaMemcpyAsync(q->host[h], q->dev[h], static_cast<size_t>(q->K * q->esize), cudaMemcpyDeviceToHost, q->s) !=
-            cudaSuccess ||
-        cudaEventRecord(q->ready[h], q->s) != cudaSuccess) {
+    if (cudaEventRecord(q->ready[h], q->s) != cudaSuccess) {
         vmt::set_last_error("vmt_scalar: refill failed");
         return VMT_ECUDA;
     }
@@ -86,9 +85,9 @@ int vmt_scalar_create(vmt_scalar** out, int variant, int lanes, uint64_t seed, u
     int rc = vmt_init(&q->st, variant, lanes, seed, jump, q->s);
     bool ok = rc == VMT_OK;
     for (int h = 0; h < 2 && ok; ++h)
-        ok = cudaHostAlloc(reinterpret_cast<void**>(&q->host[h]), static_cast<size_t>(q->K * q->esize), 0) ==
-                 cudaSuccess &&
-             cudaMalloc(&q->dev[h], static_cast<size_t>(q->K * q->esize)) == cudaSuccess &&
+        ok = cudaHostAlloc(reinterpret_cast<void**>(&q->host[h]), static_cast<size_t>(q->K * q->esize),
+                           cudaHostAllocMapped) == cudaSuccess &&
+             cudaHostGetDevicePointer(&q->mapped[h], q->host[h], 0) == cudaSuccess &&
              cudaEventCreateWithFlags(&q->ready[h], cudaEventDisableTiming) == cudaSuccess;
     if (ok) rc = refill(q.get(), 0);
     if (ok && !rc) rc = refill(q.get(), 1);
@@ -165,7 +164,6 @@ void vmt_scalar_destroy(vmt_scalar* q)
     if (q->s) cudaStreamSynchronize(q->s);
     for (int h = 0; h < 2; ++h) {
         if (q->host[h]) cudaFreeHost(q->host[h]);
-        if (q->dev[h]) cudaFree(q->dev[h]);
         if (q->ready[h]) cudaEventDestroy(q->ready[h]);
     }
     if (q->st) vmt_free(q->st);
