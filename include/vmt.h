@@ -108,7 +108,7 @@ int vmt_jump_poly(int variant, uint64_t d, int log2_extra, uint64_t* poly_out, i
 
 /*
  * vmt_prepare -- build, for the current device, every table the variant's
- * initialisation and jumps use: the characteristic polynomial (Sec. 3.2,
+ * initialisation and jumps use: the characteristic polynomial (Sec. 3.1.2,
  * found by Berlekamp-Massey or read from the cache directory), the chain
  * x^(2^q) mod it, the base-256 digit rows x^(v 256^i) of 64-bit jump offsets
  * and the rows x^(c * 1024 * n) that cut long server requests into chunks.
@@ -337,7 +337,7 @@ int vmt_stream_generate(int variant, uint64_t seed, uint64_t jump, int64_t n, in
 
 /*
  * Buffered scalar queries (the paper's scalar query mode, served from a
- * buffer; Sec. 5, scalar performance and optimised buffering).  One
+ * buffer; Sec. 4.4.1, scalar performance and optimised buffering).  One
  * V-generator (variant, lanes, seed, jump as in vmt_init) whose outputs of
  * type dtype are read one at a time on the host: the GPU's kernels write them
  * in bulk, buffer_outputs (1024 .. 2^28) at a time, directly into one of two

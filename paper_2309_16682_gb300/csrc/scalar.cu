@@ -1,6 +1,6 @@
 // scalar.cu -- buffered scalar queries (the paper's scalar query mode served
 // from a buffer: state recurrence and tempering run in bulk and single
-// outputs are read from a small buffer, Sec. 5 "Scalar Performance and
+// outputs are read from a small buffer, Sec. 4.4.1 "Scalar Performance and
 // Optimized Buffering").
 //
 // Here the bulk step is a GPU generation of K outputs of one V-generator
