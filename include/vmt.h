@@ -192,7 +192,7 @@ void vmt_batch_destroy(vmt_batch* b);
  * server that keeps up to both budgets' bytes between requests; with
  * reserve != 0 the pool takes that memory at creation (creation fails with
  * VMT_ENOMEM if the device cannot hold it), so admitted requests never wait
- * for the driver to map memory, and every variant's tables are prepared
+ * for the CUDA driver to map memory, and every variant's tables are prepared
  * (vmt_prepare) before the server accepts requests.
  * Counters: host_launch_s is the worker's host time spent issuing batches;
  * init_gpu_s sums, over finished batches, the device time from the start of

@@ -24,7 +24,7 @@ assembles the V-family stream from it:
 For SFMT19937 the interleave unit is the 128-bit element (the paper's w = 128):
 S holds uint32 sub-words and element (k, t) occupies S[4(kM + t) + j].
 
-Output conversions (not in the paper; readings recorded in the design doc):
+Output conversions (not in the paper; these are readings where it is silent):
 ``u32`` the words; ``u64`` two consecutive words, the first as the low half
 (32-bit variants) or the word itself (MT19937-64); ``f32`` (u >> 8) * 2^-24
 (32-bit words) or (u >> 40) * 2^-24 (64-bit words); ``f64``

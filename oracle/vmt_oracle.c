@@ -26,7 +26,7 @@
  * Parameters: Sec. 2.2 eq. (params) for MT19937-32, Sec. 2.3 eq. (params64)
  * for MT19937-64, Sec. 2.4 eq. (sfmt_params) for SFMT19937.
  *
- * Readings where the paper is silent (all listed in the design doc):
+ * Readings where the paper is silent:
  *   - seeding: the initialisation recurrences of the C++ standard's
  *     mersenne_twister_engine (multiplier 1812433253 for 32-bit words,
  *     6364136223846793005 for 64-bit words); SFMT uses the 32-bit one on its

@@ -133,7 +133,7 @@ struct vmt_server {
 
 namespace {
 
-// Runs on the driver's callback thread once the batch's work is done.  It
+// Runs on the CUDA runtime's callback thread once the batch's work is done.  It
 // takes no lock and makes no CUDA call: it stamps the time and raises a flag
 // that the worker picks up.
 void CUDART_CB on_batch_done(void* p)
