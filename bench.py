@@ -193,39 +193,45 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def _oracle_worker(workload, seconds, barrier, q):
-    """One host process of the all-cores oracle timing: prepare untimed, meet
-    the others at the barrier, then produce for `seconds`."""
+def _oracle_worker(workload, seconds, steps, barrier, q):
+    """One host process of the all-cores oracle timing: prepare untimed, then
+    for every step meet the others at the barrier and produce for `seconds`."""
     try:
         import oracle as O
         O.prepare_all()
         _oracle_pool(workload)
         oracle_sample(workload, 0.0, max_gens=1)
-        barrier.wait(timeout=300)
-        b, t, gens = oracle_sample(workload, seconds)
-        q.put((b, t, gens))
+        for k in range(steps):
+            barrier.wait(timeout=300)
+            b, t, gens = oracle_sample(workload, seconds)
+            q.put((k, b, t, gens))
     except Exception as e:  # reported to the parent
-        q.put(("error", repr(e), 0))
+        q.put((-1, "error", repr(e), 0))
 
 
-def oracle_sample_procs(workload: str, seconds: float, procs: int):
+def oracle_sample_procs(workload: str, seconds: float, procs: int, steps: int = 1):
     """oracle_sample in `procs` host processes at once (spawned, so safe after
-    GPU work); returns (bytes, seconds of the slowest, generators)."""
+    GPU work), `steps` times; returns [(bytes, seconds of the slowest,
+    generators)] per step."""
     import multiprocessing as mp
     import oracle as O
     O.prepare_all()                       # polynomial caches written before the workers read them
     ctx = mp.get_context("spawn")
     barrier, q = ctx.Barrier(procs), ctx.Queue()
-    ps = [ctx.Process(target=_oracle_worker, args=(workload, seconds, barrier, q)) for _ in range(procs)]
+    ps = [ctx.Process(target=_oracle_worker, args=(workload, seconds, steps, barrier, q)) for _ in range(procs)]
     for p in ps:
         p.start()
-    res = [q.get(timeout=600) for _ in ps]
+    res = [q.get(timeout=600) for _ in range(procs * steps)]
     for p in ps:
         p.join(timeout=60)
-    bad = [r for r in res if r[0] == "error"]
+    bad = [r for r in res if r[0] < 0]
     if bad:
-        raise RuntimeError(f"oracle worker failed: {bad[0][1]}")
-    return sum(r[0] for r in res), max(r[1] for r in res), sum(r[2] for r in res)
+        raise RuntimeError(f"oracle worker failed: {bad[0][2]}")
+    out = []
+    for k in range(steps):
+        rk = [r for r in res if r[0] == k]
+        out.append((sum(r[1] for r in rk), max(r[2] for r in rk), sum(r[3] for r in rk)))
+    return out
 
 
 def run_reference(args, world, rank):
@@ -239,8 +245,7 @@ def run_reference(args, world, rank):
         oracle_sample(args.workload, 0.0, max_gens=1)
     cores = host_cores()
     tot_b, tot_t, tot_g = 0, 0.0, 0
-    for _ in range(args.steps):
-        b, t, gens = oracle_sample_procs(args.workload, args.ref_seconds / max(args.steps, 1), cores)
+    for b, t, gens in oracle_sample_procs(args.workload, args.ref_seconds / max(args.steps, 1), cores, args.steps):
         tot_b += b
         tot_t += t
         tot_g += gens
@@ -520,7 +525,7 @@ def run_gb300(args, world, rank, local):
         O.prepare_all()
         _, t_pool, pool = _oracle_pool(args.workload)
         cores = host_cores()
-        b, t, gens = oracle_sample_procs(args.workload, 0.6 * args.ref_seconds, cores)
+        b, t, gens = oracle_sample_procs(args.workload, 0.6 * args.ref_seconds, cores)[0]
         b1, t1, g1 = oracle_sample(args.workload, 0.4 * args.ref_seconds)
         cpu = {"value": b / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                "single_core_value": b1 / t1 / 1e9,
