@@ -1111,14 +1111,23 @@ int vmt_jump_poly(int variant, uint64_t d, int log2_extra, uint64_t* poly_out, i
     int rc = ensure_variant(variant, nullptr);
     if (rc) return rc;
     VariantCtx& c = g_ctx[variant];
-    // x^(d 2^e) = (x^d)^(2^e): e squarings of x^d, using the stored chain for x^(2^q)
-    Poly r;
-    {
-        Poly one(1, 1);
-        r = c.mod->reduce(one);
-        for (int q = 0; q < 64; ++q)
-            if ((d >> q) & 1ull) r = c.mod->mul(r, c.chain_lo[static_cast<size_t>(q)]);
+    // x^(d 2^e) = (x^d)^(2^e): e squarings of x^d, x^d being the product of the
+    // stored chain entries x^(2^q) at the set bits q of d, multiplied as a
+    // balanced tree whose products of one level run on separate threads
+    std::vector<Poly> f;
+    for (int q = 0; q < 64; ++q)
+        if ((d >> q) & 1ull) f.push_back(c.chain_lo[static_cast<size_t>(q)]);
+    if (f.empty()) f.push_back(c.mod->reduce(Poly(1, 1)));
+    while (f.size() > 1) {
+        std::vector<Poly> g((f.size() + 1) / 2);
+        std::vector<std::thread> th;
+        for (size_t i = 0; i + 1 < f.size(); i += 2)
+            th.emplace_back([&, i]() { g[i / 2] = c.mod->mul(f[i], f[i + 1]); });
+        if (f.size() % 2) g.back() = f.back();
+        for (auto& t : th) t.join();
+        f.swap(g);
     }
+    Poly r = f[0];
     for (int i = 0; i < log2_extra; ++i) r = c.mod->sqr(r);
     const int64_t nw = static_cast<int64_t>(r.size());
     if (cap_words < nw) return fail(VMT_EINVAL, "poly_out too small");
