@@ -585,7 +585,7 @@ def main():
     ap.add_argument("--no-jump", action="store_true", help="skip the full-size jump measurement")
     ap.add_argument("--no-stream", action="store_true", help="skip the single-stream measurement")
     ap.add_argument("--no-scalar", action="store_true", help="skip the scalar-query measurement")
-    ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--serve-requests", type=int, default=100000)
     ap.add_argument("--plain-requests", type=int, default=1000)
     ap.add_argument("--generators", type=int, default=0,
                     help="smaller generator count (profiling cases); default: the workload's")
