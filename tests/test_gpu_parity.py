@@ -360,3 +360,18 @@ def test_call_longer_than_one_launch_piece(vmt, oracle_polys, variant, M, dtype)
         ref = O.vstream(variant, M, 0, L // wpo, dtype, start_word=w_at - row * row_words, lanes=lanes)
         got = _np(out[w_at // wpo: w_at // wpo + L // wpo])
         _assert_same(got, ref, f"{VNAME[variant]} word {w_at}")
+
+
+@pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])
+def test_every_jump_from_1_to_4096_equals_stepping(vmt, oracle_polys, variant):
+    """4096 single-lane generators of one seed, generator d initialised with
+    offset d (the device's digit-row jumps): each continues the base stream
+    exactly d steps in."""
+    native = "u64" if variant == O.MT64 else "u32"
+    per_step = 4 if variant == O.SFMT else 1                 # output words per recurrence step
+    d = np.arange(1, 4097, dtype=np.uint64)
+    g = vmt.VGenerator(VNAME[variant], 1, np.full(4096, 5489, np.uint64), d)
+    got = _np(g.generate(8, native))                         # [4096, 8]
+    base = O.vstream(variant, 1, 5489, (4096 + 2) * per_step + 8, native)
+    idx = (d.astype(np.int64) * per_step)[:, None] + np.arange(8)[None, :]
+    assert np.array_equal(got, base[idx])
