@@ -554,6 +554,7 @@ def run_gb300(args, world, rank, local):
                          "output_only_frac": out_bytes / (launch_ms / 1e3) / 1e9 / peak,
                          "kernel": ("gen_sfmt_kernel" if w["variant"] == "sfmt" else "gen_mt_kernel") +
                                    f"<{w['variant']}, M={w['lanes']}>"},
+            "words_per_s": sum(n * count for n, _ in segs) * args.steps * world / (total_ms / 1e3),
             "step_ms": {"best": float(np.min(per_step)), "median": float(np.median(per_step)),
                         "mean": float(np.mean(per_step))},
             "gpu_launches": args.steps,
