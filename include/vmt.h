@@ -303,6 +303,15 @@ int vmt_device_status(int reset);
  */
 int vmt_tune_set(int variant, int lanes, int threads);
 int vmt_tune_get(int variant, int lanes);
+/*
+ * vmt_tune_save / vmt_tune_load -- the tuning table as a text file, one
+ * "variant lanes threads" line per entry that differs from the default (the
+ * autotuner's results can thus be kept per GPU model and reapplied).  load
+ * applies every valid line and returns VMT_EINVAL if a line names a size that
+ * is not compiled (the valid ones still apply) or the file cannot be read.
+ */
+int vmt_tune_save(const char* path);
+int vmt_tune_load(const char* path);
 
 /*
  * vmt_tune_jump_set / vmt_tune_jump_get -- jump launches (initialisation,

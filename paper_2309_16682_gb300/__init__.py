@@ -98,6 +98,8 @@ def lib() -> ctypes.CDLL:
             "vmt_server_destroy": (None, [P]),
             "vmt_tune_set": (I, [I, I, I]),
             "vmt_tune_get": (I, [I, I]),
+            "vmt_tune_save": (I, [ctypes.c_char_p]),
+            "vmt_tune_load": (I, [ctypes.c_char_p]),
             "vmt_tune_jump_set": (I, [I, I64]),
             "vmt_measure_store_bw": (I, [I64, I, P, P]),
             "vmt_stream_generate": (I, [I, U64, U64, I64, I, P, P]),
@@ -380,6 +382,24 @@ def tune_jump(variant: str, split_below: int | None = None) -> int:
     if split_below is not None:
         _check(lib().vmt_tune_jump_set(VARIANTS[variant], int(split_below)))
     return old
+
+
+def tune_save(path: str) -> None:
+    """Write the tuning table (entries that differ from the defaults)."""
+    _check(lib().vmt_tune_save(os.fspath(path).encode()))
+
+
+def tune_load(path: str) -> None:
+    """Apply a tuning table written by tune_save."""
+    _check(lib().vmt_tune_load(os.fspath(path).encode()))
+
+
+def tune_cache_path() -> str:
+    """Where the autotuner's table is kept for the current GPU model."""
+    import re
+    import torch
+    name = re.sub(r"[^A-Za-z0-9]+", "_", torch.cuda.get_device_name())
+    return os.path.join(CACHE_DIR, f"tune_{name}.txt")
 
 
 def tune_get(variant: str, lanes: int) -> int:

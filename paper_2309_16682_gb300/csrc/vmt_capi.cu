@@ -1604,6 +1604,39 @@ int vmt_tune_get(int variant, int lanes)
     return vmt::tuned_threads(variant, lanes);
 }
 
+int vmt_tune_save(const char* path)
+{
+    if (!path) return fail(VMT_EINVAL, "null path");
+    FILE* f = std::fopen(path, "w");
+    if (!f) return fail(VMT_EINVAL, std::string("cannot write ") + path);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_lock);
+        read_tune_env_locked();
+        std::fprintf(f, "# variant lanes threads\n");
+        for (int v = 0; v < 3; ++v)
+            for (int m = 1; m <= 16; m *= 2)
+                if (g_tune_threads[v][m]) std::fprintf(f, "%d %d %d\n", v, m, g_tune_threads[v][m]);
+    }
+    const bool ok = std::fclose(f) == 0;
+    return ok ? VMT_OK : fail(VMT_EINVAL, std::string("cannot write ") + path);
+}
+
+int vmt_tune_load(const char* path)
+{
+    if (!path) return fail(VMT_EINVAL, "null path");
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(VMT_EINVAL, std::string("cannot read ") + path);
+    char line[128];
+    int bad = 0;
+    while (std::fgets(line, sizeof(line), f)) {
+        if (line[0] == '#' || line[0] == '\n') continue;
+        int v = -1, m = 0, t = -1;
+        if (std::sscanf(line, "%d %d %d", &v, &m, &t) != 3 || vmt_tune_set(v, m, t) != VMT_OK) ++bad;
+    }
+    std::fclose(f);
+    return bad ? fail(VMT_EINVAL, "tuning file has entries that match no compiled kernel") : VMT_OK;
+}
+
 int vmt_autotune(int variant, int lanes, int64_t count, int64_t n_per_gen, int dtype, int reps, void* cuda_stream,
                  int* best_threads, double* best_ms)
 {

@@ -103,3 +103,24 @@ def test_library_full_chain_matches_oracle(L, oracle_polys):
     for i, q in enumerate(range(19933, 19938)):
         assert np.array_equal(got[i], O.x2pow(O.MT64, q)[:313]), q
     assert time.time() - t < 120
+
+
+def test_tuning_table_round_trips_through_a_file(L, tmp_path):
+    import paper_2309_16682_gb300 as vmt
+    old = vmt.tune_get("mt32", 16)
+    try:
+        vmt.tune_set("mt32", 16, 1024)
+        f = tmp_path / "tune.txt"
+        vmt.tune_save(f)
+        vmt.tune_set("mt32", 16, 0)
+        assert vmt.tune_get("mt32", 16) != 1024
+        vmt.tune_load(f)
+        assert vmt.tune_get("mt32", 16) == 1024
+        bad = tmp_path / "bad.txt"
+        bad.write_text("0 16 777\n0 8 512\n")
+        with pytest.raises(vmt.VMTError):
+            vmt.tune_load(bad)                   # 777 threads is not compiled...
+        assert vmt.tune_get("mt32", 8) == 512    # ...but the valid line applied
+    finally:
+        vmt.tune_set("mt32", 16, old if old in (512, 1024) else 0)
+        vmt.tune_set("mt32", 8, 0)
