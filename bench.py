@@ -379,10 +379,9 @@ def run_gb300(args, world, rank, local):
     outs = [torch.empty((count, n), dtype=vmt._torch_dtype(dt), device="cuda") for n, dt in segs]
     tuned = None
     if args.tune:
-        # the autotuner times each compiled CTA size on this workload's size (a
-        # smaller slice can favour a CTA size that loses at full occupancy)
-        n_tune = sum(n for n, _ in segs)
-        tuned = vmt.autotune(w["variant"], w["lanes"], count, n_tune, segs[0][1], reps=3)
+        # the autotuner times each compiled CTA size on this workload: its size
+        # and its fused output mix (both change which size wins)
+        tuned = vmt.autotune(w["variant"], w["lanes"], count, 0, reps=3, segments=segs)
         vmt.tune_save(vmt.tune_cache_path())   # kept per GPU model; vmt.tune_load reapplies it
     tune_threads = vmt.tune_get(w["variant"], w["lanes"])
     traffic_key = ("gen_sfmt_kernel" if w["variant"] == "sfmt" else "gen_mt_kernel") + f"<{w['variant']}, M={w['lanes']}>"

@@ -392,6 +392,10 @@ int vmt_measure_store_bw(int64_t bytes, int reps, double* best_gbs, void* cuda_s
 int vmt_selftest_wait(int64_t limit_ns, int64_t* elapsed_ns);
 int vmt_autotune(int variant, int lanes, int64_t count, int64_t n_per_gen, int dtype, int reps, void* cuda_stream,
                  int* best_threads, double* best_ms);
+/* as vmt_autotune, timing vmt_generate_multi on the caller's own segment list
+ * (the table is keyed by variant and lanes, so tune with the mix you run) */
+int vmt_autotune_multi(int variant, int lanes, int64_t count, int nseg, const int64_t* counts, const int* dtypes,
+                       int reps, void* cuda_stream, int* best_threads, double* best_ms);
 
 /* Release a state object (NULL is allowed). */
 void vmt_free(vmt_state* st);

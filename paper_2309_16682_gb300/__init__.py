@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
             "vmt_stream_generate": (I, [I, U64, U64, I64, I, P, P]),
             "vmt_tune_jump_get": (I64, [I]),
             "vmt_autotune": (I, [I, I, I64, I64, I, I, P, P, P]),
+            "vmt_autotune_multi": (I, [I, I, I64, I, P, P, I, P, P, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -406,12 +407,21 @@ def tune_get(variant: str, lanes: int) -> int:
     return _check(lib().vmt_tune_get(VARIANTS[variant], int(lanes)))
 
 
-def autotune(variant: str, lanes: int, count: int, n_per_gen: int, dtype: str = "u32", reps: int = 3, stream=None):
-    """Time every compiled CTA size and keep the fastest; returns (threads, ms per call)."""
+def autotune(variant: str, lanes: int, count: int, n_per_gen: int, dtype: str = "u32", reps: int = 3, stream=None,
+             segments=None):
+    """Time every compiled CTA size and keep the fastest; returns (threads, ms
+    per call).  `segments` [(n, dtype), ...] times that fused output mix
+    instead of n_per_gen outputs of one type."""
     t = ctypes.c_int(0)
     ms = ctypes.c_double(0.0)
-    _check(lib().vmt_autotune(VARIANTS[variant], int(lanes), int(count), int(n_per_gen), DTYPES[dtype], int(reps),
-                              _stream_handle(stream), ctypes.byref(t), ctypes.byref(ms)))
+    if segments:
+        counts = (ctypes.c_int64 * len(segments))(*[int(n) for n, _ in segments])
+        dts = (ctypes.c_int * len(segments))(*[DTYPES[d] for _, d in segments])
+        _check(lib().vmt_autotune_multi(VARIANTS[variant], int(lanes), int(count), len(segments), counts, dts,
+                                        int(reps), _stream_handle(stream), ctypes.byref(t), ctypes.byref(ms)))
+    else:
+        _check(lib().vmt_autotune(VARIANTS[variant], int(lanes), int(count), int(n_per_gen), DTYPES[dtype],
+                                  int(reps), _stream_handle(stream), ctypes.byref(t), ctypes.byref(ms)))
     return t.value, ms.value
 
 

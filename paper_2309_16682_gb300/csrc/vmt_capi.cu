@@ -1637,11 +1637,14 @@ int vmt_tune_load(const char* path)
     return bad ? fail(VMT_EINVAL, "tuning file has entries that match no compiled kernel") : VMT_OK;
 }
 
-int vmt_autotune(int variant, int lanes, int64_t count, int64_t n_per_gen, int dtype, int reps, void* cuda_stream,
-                 int* best_threads, double* best_ms)
+int vmt_autotune_multi(int variant, int lanes, int64_t count, int nseg, const int64_t* counts, const int* dtypes,
+                       int reps, void* cuda_stream, int* best_threads, double* best_ms)
 {
-    if (!valid_variant(variant) || !valid_lanes(lanes) || count < 1 || n_per_gen < 1 || reps < 1)
+    if (!valid_variant(variant) || !valid_lanes(lanes) || count < 1 || reps < 1 || nseg < 1 || nseg > VMT_MAXSEG ||
+        !counts || !dtypes)
         return fail(VMT_EINVAL, "bad autotune arguments");
+    for (int i = 0; i < nseg; ++i)
+        if (counts[i] < 1 || dtypes[i] < VMT_U32 || dtypes[i] > VMT_F64) return fail(VMT_EINVAL, "bad autotune segment");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const auto cands = tune_candidates(variant, lanes);
     std::vector<uint64_t> seeds(static_cast<size_t>(count));
@@ -1649,49 +1652,65 @@ int vmt_autotune(int variant, int lanes, int64_t count, int64_t n_per_gen, int d
     vmt_state* st = nullptr;
     int rc = vmt_init_batch(&st, variant, lanes, count, seeds.data(), nullptr, cuda_stream);
     if (rc) return rc;
-    void* out = nullptr;
-    const size_t bytes = static_cast<size_t>(count * n_per_gen * elem_bytes(dtype));
-    if (cudaMalloc(&out, bytes) != cudaSuccess) {
-        vmt_free(st);
-        return fail(VMT_ENOMEM, "autotune output buffer");
-    }
+    std::vector<void*> outs(static_cast<size_t>(nseg), nullptr);
+    for (int i = 0; i < nseg; ++i)
+        if (cudaMalloc(&outs[static_cast<size_t>(i)], static_cast<size_t>(count * counts[i] * elem_bytes(dtypes[i]))) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            for (void* o : outs)
+                if (o) cudaFree(o);
+            vmt_free(st);
+            return fail(VMT_ENOMEM, "autotune output buffer");
+        }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    const std::vector<int> tried = cands.empty() ? std::vector<int>{0} : cands;
+    // two alternating rounds over the candidates, each candidate's time the
+    // mean of `reps` calls after a warm-up; a candidate keeps its better round
+    std::vector<double> t_best(tried.size(), 1e30);
+    for (int round = 0; round < 2 && rc == VMT_OK; ++round)
+        for (size_t k = 0; k < tried.size() && rc == VMT_OK; ++k) {
+            {
+                std::lock_guard<std::mutex> lk(g_tune_lock);
+                g_tune_threads[variant][lanes] = tried[k];
+            }
+            rc = vmt_generate_multi(st, nseg, counts, dtypes, outs.data(), cuda_stream);   // warm-up
+            if (rc) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && rc == VMT_OK; ++r)
+                rc = vmt_generate_multi(st, nseg, counts, dtypes, outs.data(), cuda_stream);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t_best[k] = std::min(t_best[k], static_cast<double>(ms) / reps);
+        }
     int best = 0;
     double best_t = 1e30;
-    const std::vector<int> tried = cands.empty() ? std::vector<int>{0} : cands;
-    for (int threads : tried) {
-        {
-            std::lock_guard<std::mutex> lk(g_tune_lock);
-            g_tune_threads[variant][lanes] = threads;
+    for (size_t k = 0; k < tried.size(); ++k)
+        if (t_best[k] < best_t) {
+            best_t = t_best[k];
+            best = tried[k];
         }
-        rc = vmt_generate(st, n_per_gen, dtype, out, cuda_stream);   // warm-up
-        if (rc) break;
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && rc == VMT_OK; ++r) rc = vmt_generate(st, n_per_gen, dtype, out, cuda_stream);
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rc) break;
-        if (ms / reps < best_t) {
-            best_t = ms / reps;
-            best = threads;
-        }
-    }
     {
         std::lock_guard<std::mutex> lk(g_tune_lock);
         g_tune_threads[variant][lanes] = best;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(out);
+    for (void* o : outs) cudaFree(o);
     vmt_free(st);
     if (rc) return rc;
     if (best_threads) *best_threads = best;
     if (best_ms) *best_ms = best_t;
     return VMT_OK;
+}
+
+int vmt_autotune(int variant, int lanes, int64_t count, int64_t n_per_gen, int dtype, int reps, void* cuda_stream,
+                 int* best_threads, double* best_ms)
+{
+    return vmt_autotune_multi(variant, lanes, count, 1, &n_per_gen, &dtype, reps, cuda_stream, best_threads, best_ms);
 }
 
 int vmt_poly_minpoly(const uint64_t* bits, int64_t n, uint64_t* mu_out, int64_t cap_words)

@@ -60,6 +60,7 @@ def test_invalid_arguments_rejected(L):
     assert L.vmt_scalar_create(ctypes.byref(h), 0, 4, 1, 0, 0, 10) == vmt.VMT_EINVAL    # buffer too small
     assert L.vmt_scalar_next(None, None) == vmt.VMT_EINVAL
     assert L.vmt_server_next_done(None, 0, None) == vmt.VMT_EINVAL
+    assert L.vmt_autotune_multi(0, 16, 10, 0, None, None, 1, None, None, None) == vmt.VMT_EINVAL
 
 
 @pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])

@@ -375,3 +375,17 @@ def test_every_jump_from_1_to_4096_equals_stepping(vmt, oracle_polys, variant):
     base = O.vstream(variant, 1, 5489, (4096 + 2) * per_step + 8, native)
     idx = (d.astype(np.int64) * per_step)[:, None] + np.arange(8)[None, :]
     assert np.array_equal(got, base[idx])
+
+
+def test_autotuner_picks_a_compiled_size_and_keeps_results_exact(vmt):
+    old = vmt.tune_get("mt32", 16)
+    try:
+        t, ms = vmt.autotune("mt32", 16, 512, 0, reps=2, segments=[(3000, "u32"), (3000, "f32")])
+        assert t in (512, 1024) and ms > 0 and vmt.tune_get("mt32", 16) == t
+        seeds = I.splitmix64(11, 4)
+        a = _np(vmt.VGenerator("mt32", 16, seeds).generate(5000, "u32"))
+        vmt.tune_set("mt32", 16, 1024 if t == 512 else 512)
+        b = _np(vmt.VGenerator("mt32", 16, seeds).generate(5000, "u32"))
+        assert np.array_equal(a, b)
+    finally:
+        vmt.tune_set("mt32", 16, old if old in (512, 1024) else 0)
