@@ -594,11 +594,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
-    world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
+        # host-only: no process group; under torchrun rank 0 alone runs it
+        from paper_2309_16682_gb300 import shard
+        world, rank, _ = shard.env_world()
         run_reference(args, world, rank)
-    else:
-        run_gb300(args, world, rank, local)
+        return
+    world, rank, local = dist_setup(args.gpus)
+    run_gb300(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
