@@ -231,6 +231,38 @@ def test_full_workloads_sampled(vmt, oracle_polys, name):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("name", ["vmt32_m16_g65536", "vmt64_m8_g32768", "vsfmt_m4_g16384"])
+def test_full_workloads_wide_sample(vmt, oracle_polys, name):
+    """1024 seeded random generators plus the first and the last of each
+    full-size workload: the first two blocks of each (every lane's jump-ahead
+    and the interleave) equal the oracle.  The lane polynomials x^(tJ) are
+    the same for every generator, so the oracle computes them once."""
+    w = I.WORKLOADS[name]
+    variant, M = VID[w["variant"]], w["lanes"]
+    seeds = I.workload_seeds(name)
+    count = w["generators"]
+    g = vmt.VGenerator(w["variant"], M, seeds)
+    native = "u64" if variant == O.MT64 else "u32"
+    words = 2 * M * {O.MT32: 624, O.MT64: 312, O.SFMT: 624}[variant]
+    out = g.generate(words, native)
+    rng = np.random.default_rng(2309 + len(name))
+    sample = sorted({0, count - 1} | {int(x) for x in rng.choice(count, 1024, replace=False)})
+    signed = out.view(torch.int64 if native == "u64" else torch.int32)   # unsigned CUDA indexing is missing
+    got = signed[torch.as_tensor(sample, device=out.device)].cpu().numpy().view(
+        np.uint64 if native == "u64" else np.uint32)
+    # the plain oracle takes up to ~0.7 s per generator: one spawned process per host core
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+
+    from helpers.oracle_pool import first_words
+    tasks = [(variant, M, int(seeds[gi]), words) for gi in sample]
+    with ProcessPoolExecutor(max_workers=len(os.sched_getaffinity(0)), mp_context=mp.get_context("spawn")) as ex:
+        refs = list(ex.map(first_words, tasks, chunksize=4))
+    for row, (gi, ref) in enumerate(zip(sample, refs)):
+        _assert_same(got[row], ref, f"{name} gen {gi}")
+
+
 @pytest.mark.parametrize("variant,M,threads", [("mt32", 16, 1024), ("mt32", 8, 512), ("mt64", 8, 512),
                                                ("mt64", 16, 1024)])
 def test_every_cta_size_gives_the_same_stream(vmt, variant, M, threads):
