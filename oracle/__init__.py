@@ -31,8 +31,9 @@ Output conversions (not in the paper; these are readings where it is silent):
 ((a >> 5) * 2^26 + (b >> 6)) * 2^-53 from two consecutive 32-bit words, or
 (u >> 11) * 2^-53 from one 64-bit word.
 
-Parity unpinned: SFMT19937 seeding (no published output vector available);
-every other function is pinned in tests/test_oracle_*.py.
+Every function is pinned in tests/test_oracle_*.py.  SFMT19937 seeding is
+pinned to numpy's MT19937 legacy seeding over its 624 sub-words; against
+upstream SFMT output vectors it is parity unpinned (none available).
 """
 from __future__ import annotations
 

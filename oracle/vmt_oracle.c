@@ -43,8 +43,10 @@
  * jump is pinned by brute-force stepping and numpy's MT19937.jumped().
  * SFMT19937: the recurrence is pinned algebraically (its minimal polynomial
  * must carry a primitive factor of degree 19937) and the certification by
- * its defining properties; SFMT seeding has no published vector in reach and
- * is "parity unpinned".
+ * its defining properties; SFMT seeding (the 32-bit initialisation over the
+ * 624 sub-words) is pinned by numpy's MT19937 key array after its legacy
+ * seeding.  Whether that reading matches upstream SFMT output vectors has no
+ * published vector in reach: "parity unpinned" in that sense only.
  */
 #include <stdint.h>
 #include <stdlib.h>

@@ -121,20 +121,43 @@ def test_sfmt_certified_seeds_have_odd_parity():
         assert O.sfmt_inner(O.seed_state(O.SFMT, s)) == 1
 
 
-def test_sfmt_certification_flips_only_bit0_when_needed():
-    """With the parity vector's lowest set bit at sub-word 0 bit 0, certification
-    changes at most that one bit of the seeded buffer."""
-    import ctypes
-    for s in range(40):
-        st = O.seed_state(O.SFMT, s)
-        raw = np.zeros(624, np.uint32)
-        raw[0] = s
-        for i in range(1, 624):
-            raw[i] = (1812433253 * (int(raw[i - 1]) ^ (int(raw[i - 1]) >> 30)) + i) & 0xFFFFFFFF
-        diff = st.words ^ raw
-        assert np.count_nonzero(diff) <= 1
-        if np.count_nonzero(diff):
-            assert diff[0] == 1
+def _numpy_mt_key(seed):
+    """The 624-word array numpy's own MT19937 holds right after its legacy
+    integer seeding (the 32-bit initialisation that SFMT19937 also runs over
+    its 624 sub-words, element k being sub-words 4k..4k+3)."""
+    bg = np.random.MT19937()
+    bg._legacy_seeding(seed)
+    st = bg.state["state"]
+    assert st["pos"] == 624
+    return np.asarray(st["key"], dtype=np.uint32)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 1234, 5489, 2**31, 2**32 - 1])
+def test_sfmt_seeding_is_numpy_mt_key_up_to_certification(seed):
+    """Seeded SFMT buffer = numpy's MT19937 key array, except for the one bit
+    that certification may flip: the parity vector's lowest set bit, sub-word 0
+    bit 0.  The flip happens exactly when the key array fails the check."""
+    key = _numpy_mt_key(seed)
+    st = O.seed_state(O.SFMT, seed)
+    assert st.k == 0
+    diff = st.words ^ key
+    assert np.count_nonzero(diff[1:]) == 0
+    assert diff[0] in (0, 1)
+    key_parity = O.sfmt_inner(O.State(O.SFMT, key, 0))
+    assert diff[0] == (1 - key_parity)
+    assert O.sfmt_inner(st) == 1
+
+
+def test_sfmt_certification_flips_when_needed():
+    """Over many seeds both outcomes occur (an even key array is fixed, an odd
+    one is left alone), so the test above exercises both branches."""
+    flipped = [int((O.seed_state(O.SFMT, s).words ^ _numpy_mt_key(s))[0]) for s in range(64)]
+    assert 0 < sum(flipped) < 64
+
+
+def test_sfmt_64bit_seed_taken_mod_2_32():
+    for s in [7, 2**32 - 1]:
+        assert np.array_equal(O.seed_state(O.SFMT, s + (5 << 32)).words, O.seed_state(O.SFMT, s).words)
 
 
 def test_splitmix64_two_forms_and_published_first_value():
