@@ -125,3 +125,23 @@ def test_tuning_table_round_trips_through_a_file(L, tmp_path):
     finally:
         vmt.tune_set("mt32", 16, old if old in (512, 1024) else 0)
         vmt.tune_set("mt32", 8, 0)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without libvmt.so every call raises: there is no CPU fallback."""
+    import subprocess
+    import sys
+    code = (
+        "import paper_2309_16682_gb300 as v\n"
+        f"v.LIB_PATH = {str(tmp_path / 'absent' / 'libvmt.so')!r}\n"
+        "for f in (v.lib, lambda: v.jump_poly('mt32', 5), lambda: v.VGenerator('mt32', 4, [1])):\n"
+        "    try:\n"
+        "        f()\n"
+        "    except RuntimeError as e:\n"
+        "        assert 'is missing' in str(e), e\n"
+        "    else:\n"
+        "        raise SystemExit('call succeeded without the library')\n"
+        "print('ok')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip() == "ok"
