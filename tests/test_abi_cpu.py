@@ -88,12 +88,14 @@ def test_library_mulmod_matches_oracle(L, oracle_polys):
             assert np.array_equal(got, ref[:nw + 1])
 
 
-def test_library_chain_matches_oracle(L, oracle_polys):
-    mu = O.minpoly(O.MT32)
-    nw = 313
+@pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])
+def test_library_chain_matches_oracle(L, oracle_polys, variant):
+    mu = O.minpoly(variant)
+    nw = O.poly_deg(mu) // 64 + 1
     got = vmt.poly_x2pow(mu[:nw], 0, 80)
     for q in (0, 1, 5, 31, 64, 80):
-        assert np.array_equal(got[q], O.x2pow(O.MT32, q)[:nw]), q
+        ref = O.x2pow(variant, q)
+        assert np.array_equal(got[q], ref[:nw]) and not ref[nw:].any(), q
 
 
 @pytest.mark.slow
