@@ -275,6 +275,14 @@ def _pct(x, q):
     return float(np.percentile(np.asarray(x), q)) if len(x) else None
 
 
+def _ms(x, q):
+    v = _pct(x, q)
+    return None if v is None else 1e3 * v
+
+
+SMALL_N = 10_000        # "small" requests: at most this many outputs
+
+
 def run_served(vmt, requests: int, rate: float, plain_requests: int):
     import torch
     tr = I.request_trace(requests, rate_per_s=rate)
@@ -294,7 +302,7 @@ def run_served(vmt, requests: int, rate: float, plain_requests: int):
     # one client thread: submit each request at its arrival time, and between
     # arrivals take finished requests from the completion queue, read their
     # latency (stamped by the server) and release them
-    lat, lag = [], {}
+    lat, lat_n, lag, nreq = [], [], {}, {}
     t0 = time.perf_counter()
     i, done, t_end = 0, 0, t0
     while done < requests:
@@ -303,11 +311,13 @@ def run_served(vmt, requests: int, rate: float, plain_requests: int):
             v, m, dt, seed, jump, n, arr = reqs[i]
             rid = srv.submit(v, m, dt, seed, jump, n)
             lag[rid] = max(0.0, time.perf_counter() - t0 - arr)   # submitted this late after its arrival
+            nreq[rid] = n
             i += 1
         wait_us = int(1e6 * (reqs[i][6] - now)) if i < requests else 20000
         rid = srv.next_done(max(0, min(wait_us, 20000)))
         while rid is not None:
             lat.append(srv.poll(rid)[3] + lag.pop(rid))
+            lat_n.append(nreq.pop(rid))
             srv.release(rid)
             done += 1
             t_end = time.perf_counter()
@@ -316,7 +326,9 @@ def run_served(vmt, requests: int, rate: float, plain_requests: int):
     stats0 = warm_stats
     srv.close()
     total_bytes = sum(n * esize[dt] for (_, _, dt, _, _, n, _) in reqs)
-    batched = {"p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99),
+    small = [t for t, n in zip(lat, lat_n) if n <= SMALL_N]
+    batched = {"p50_ms": _ms(lat, 50), "p99_ms": _ms(lat, 99),
+               "small_n_p50_ms": _ms(small, 50), "small_n_requests": len(small),
                "throughput_GBps": total_bytes / (t_end - t0) / 1e9, "batches": stats["batches"],
                "peak_output_bytes": stats["peak_output_bytes"], "wall_s": t_end - t0,
                "host_launch_s": stats["host_launch_s"] - stats0["host_launch_s"],
@@ -324,7 +336,7 @@ def run_served(vmt, requests: int, rate: float, plain_requests: int):
                "batch_gpu_s": stats["batch_gpu_s"] - stats0["batch_gpu_s"]}
     # plain form on the first plain_requests requests of the same trace
     pr = reqs[:plain_requests]
-    plat = []
+    plat, psmall = [], []
     pbytes = 0
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
@@ -335,17 +347,21 @@ def run_served(vmt, requests: int, rate: float, plain_requests: int):
         out = g.generate(n, dt)
         stream.synchronize()
         plat.append(time.perf_counter() - t0 - arr)
+        if n <= SMALL_N:
+            psmall.append(plat[-1])
         pbytes += n * esize[dt]
         g.close()
         del out
     p_wall = time.perf_counter() - t0
-    plain = {"p50_ms": 1e3 * _pct(plat, 50), "p99_ms": 1e3 * _pct(plat, 99), "throughput_GBps": pbytes / p_wall / 1e9,
+    plain = {"p50_ms": _ms(plat, 50), "p99_ms": _ms(plat, 99), "throughput_GBps": pbytes / p_wall / 1e9,
+             "small_n_p50_ms": _ms(psmall, 50), "small_n_requests": len(psmall),
              "requests": len(pr), "wall_s": p_wall}
     return {"requests": requests, "arrival_rate_per_s": rate, "lanes": "4/8/16", "length_words": "log-uniform 1e3..1e8",
             "batched": batched, "plain": plain,
             "note": "latency = the trace's arrival time to completion (server-stamped), outputs released in completion "
                     "order by a single client thread; plain = one request at a time, "
-                    "vmt_init + vmt_generate + synchronise, on a prefix of the same trace"}
+                    "vmt_init + vmt_generate + synchronise, on a prefix of the same trace; small_n = requests "
+                    "of at most 10^4 outputs"}
 
 
 # ---------------------------------------------------------------------------
@@ -513,6 +529,7 @@ def run_gb300(args, world, rank, local):
         sq_s = time.perf_counter() - t0
         sq.close()
         scalar = {"value": nq / sq_s, "unit": "queries/s", "queries": nq, "seconds": sq_s,
+                  "ms_per_1e4_queries": 1e3 * SMALL_N * sq_s / nq,
                   "note": "vmt_scalar_drain: one u32 per query from a 16-lane MT32 V-generator, buffers of 2^22 "
                           "outputs refilled by the GPU while the host reads the other one"}
 
