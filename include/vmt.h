@@ -176,7 +176,11 @@ void vmt_batch_destroy(vmt_batch* b);
  * as they arrive, at most max_batch (1..4096) per batch: batched seeding and
  * jump-ahead on one stream, a persistent ragged generation (longest first) on
  * another, so a new batch's initialisation overlaps the previous batch's
- * generation.
+ * generation.  Requests of at most 16,384 outputs may also go ahead of the
+ * queue, in batches of their own on an extra slot with high-priority streams;
+ * their outputs count against an express budget of output_budget_bytes / 16
+ * instead of the output budget, and they pass a waiting request only where it
+ * would still fit the state budget afterwards.
  *   vmt_server_submit   never blocks; *id names the request
  *   vmt_server_poll     status VMT_SERVER_QUEUED / RUNNING / DONE or a negative
  *                       VMT_E* code (that request failed; the server goes on);

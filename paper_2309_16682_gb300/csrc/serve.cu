@@ -15,6 +15,14 @@
 // (HBM-bound stores).  Completion is signalled from the stream by a host
 // function that stamps the requests' completion times.
 //
+// Requests of at most kExpressOutputs outputs may also go ahead of the queue
+// in a batch of their own on a fifth slot, whose generation stream has the
+// high priority of the init streams: their latency is then a few short
+// launches, not the queue plus a batch of long requests.  Their outputs count
+// against an express budget (a sixteenth of the output budget), so they never
+// take output memory that a waiting request needs; they pass others only where
+// the first request they pass still fits the state budget afterwards.
+//
 // Failure handling, all on the host: a request that can never fit the budgets
 // or has invalid parameters fails alone (status < 0) and the server goes on;
 // vmt_server_wait gives up after its timeout with VMT_ETIMEOUT; destroying the
@@ -58,7 +66,10 @@ int64_t n_chunks(int variant, int lanes, int64_t w)
     return std::min<int64_t>((w + C - 1) / C, vmt::kChunkRows + 1);
 }
 
-constexpr int kSlots = 4;          // batches that may be in flight at once
+constexpr int kSlots = 5;          // batches that may be in flight at once
+constexpr int kExpress = kSlots - 1;   // the slot kept for small requests only
+constexpr int64_t kExpressOutputs = 16384;   // "small": at most this many outputs
+constexpr size_t kExpressScan = 4096;        // queue entries an express batch looks at
 constexpr int kMaxGroups = 16;     // kernels per batch
 constexpr int kMaxUnits = 65536;   // units (requests or chunks of requests) per batch
 
@@ -71,6 +82,7 @@ struct Req {
     int64_t chunks = 1;      // generators it runs on (one per chunk)
     int launch_rc = VMT_OK;  // set when its own launch step failed (it fails alone)
     bool admitted = false;   // its output bytes count against the budget
+    bool express = false;    // ... against the express budget
     double t_submit = 0, t_done = 0;
 };
 
@@ -117,6 +129,7 @@ struct vmt_server {
     std::deque<Batch*> inflight;
     Slot slots[kSlots];
     int64_t used_state = 0, used_out = 0, peak_state = 0, peak_out = 0;
+    int64_t used_out_express = 0;   // outputs of express requests (budget: output budget / 16)
     int64_t batches = 0, completed = 0, failed = 0, bytes_out = 0;
     double host_launch_s = 0, init_gpu_s = 0, batch_gpu_s = 0;
     int64_t cancelled = 0;
@@ -347,18 +360,66 @@ void worker_main(vmt_server* s)
             for (int i : done_slots) s->slots[i].busy = false;
         }
         if (s->stop && s->queue.empty() && s->inflight.empty()) break;
-        int slot = -1;
-        for (int i = 0; i < kSlots; ++i)
-            if (!s->slots[i].busy) {
-                slot = i;
-                break;
-            }
-        // admission: FIFO, as long as both budgets hold
         std::vector<Req*> rq;
         std::vector<uint64_t> ids;
         std::map<std::tuple<int, int, int>, int> kinds;
         int64_t add_state = 0, units = 0;
-        while (slot >= 0 && !s->queue.empty() && static_cast<int>(rq.size()) < s->cfg.max_batch) {
+        // false when the request would exceed a batch limit (kernel groups, units)
+        auto fits_batch = [&](const Req& q) {
+            const auto key = std::make_tuple(q.r.variant, q.r.lanes, q.r.dtype);
+            if (!kinds.count(key) && static_cast<int>(kinds.size()) == kMaxGroups) return false;
+            return units + q.chunks <= kMaxUnits;
+        };
+        auto admit = [&](Req& q, uint64_t id, bool express) {
+            units += q.chunks;
+            kinds[std::make_tuple(q.r.variant, q.r.lanes, q.r.dtype)] = 1;
+            add_state += q.state_bytes;
+            (express ? s->used_out_express : s->used_out) += q.bytes;
+            q.admitted = true;
+            q.express = express;
+            q.status = VMT_SERVER_RUNNING;
+            rq.push_back(&q);
+            ids.push_back(id);
+        };
+        int slot = -1;
+        if (!s->slots[kExpress].busy) {
+            // express batch: small requests go ahead of the queue on a slot of
+            // their own, so that they never wait behind long ones.  Their
+            // outputs count against an express budget of their own; the first
+            // queued request they pass keeps its claim on the state budget: a
+            // small request goes ahead only if that one would still fit after it.
+            const int64_t express_budget = s->cfg.output_budget_bytes / 16;
+            int64_t claim_state = 0;
+            bool claimed = false;
+            for (size_t k = 0; k < s->queue.size() && k < kExpressScan &&
+                               static_cast<int>(rq.size()) < s->cfg.max_batch;) {
+                const uint64_t id = s->queue[k];
+                Req& q = s->reqs[id];
+                const bool never = q.state_bytes > s->cfg.state_budget_bytes || q.bytes > s->cfg.output_budget_bytes;
+                if (never || q.r.n > kExpressOutputs || q.bytes > express_budget) {
+                    if (!never && !claimed) {
+                        claimed = true;
+                        claim_state = q.state_bytes;
+                    }
+                    ++k;
+                    continue;
+                }
+                if (s->used_state + add_state + q.state_bytes + claim_state > s->cfg.state_budget_bytes ||
+                    s->used_out_express + q.bytes > express_budget || !fits_batch(q))
+                    break;
+                admit(q, id, true);
+                s->queue.erase(s->queue.begin() + static_cast<std::ptrdiff_t>(k));
+            }
+            if (!rq.empty()) slot = kExpress;
+        }
+        if (slot < 0)
+            for (int i = 0; i < kExpress; ++i)
+                if (!s->slots[i].busy) {
+                    slot = i;
+                    break;
+                }
+        // admission: FIFO, as long as both budgets hold
+        while (slot >= 0 && slot != kExpress && !s->queue.empty() && static_cast<int>(rq.size()) < s->cfg.max_batch) {
             const uint64_t id = s->queue.front();
             Req& q = s->reqs[id];
             if (q.state_bytes > s->cfg.state_budget_bytes || q.bytes > s->cfg.output_budget_bytes) {
@@ -370,19 +431,9 @@ void worker_main(vmt_server* s)
                 continue;
             }
             if (s->used_state + add_state + q.state_bytes > s->cfg.state_budget_bytes ||
-                s->used_out + q.bytes > s->cfg.output_budget_bytes)
+                s->used_out + q.bytes > s->cfg.output_budget_bytes || !fits_batch(q))
                 break;
-            const auto key = std::make_tuple(q.r.variant, q.r.lanes, q.r.dtype);
-            if (!kinds.count(key) && static_cast<int>(kinds.size()) == kMaxGroups) break;
-            if (units + q.chunks > kMaxUnits) break;
-            units += q.chunks;
-            kinds[key] = 1;
-            add_state += q.state_bytes;
-            s->used_out += q.bytes;
-            q.admitted = true;
-            q.status = VMT_SERVER_RUNNING;
-            rq.push_back(&q);
-            ids.push_back(id);
+            admit(q, id, false);
             s->queue.pop_front();
         }
         if (rq.empty()) {
@@ -393,7 +444,7 @@ void worker_main(vmt_server* s)
         }
         s->used_state += add_state;
         s->peak_state = std::max(s->peak_state, s->used_state);
-        s->peak_out = std::max(s->peak_out, s->used_out);
+        s->peak_out = std::max(s->peak_out, s->used_out + s->used_out_express);
         Batch* b = new Batch();
         b->slot = slot;
         b->ids = ids;
@@ -454,8 +505,9 @@ int vmt_server_create(vmt_server** out, const vmt_server_config* cfg)
         const size_t n = static_cast<size_t>(cfg->max_batch);
         const size_t nu = static_cast<size_t>(kMaxUnits);
         // initialisation (short jump launches) is scheduled ahead of generation
-        // blocks still waiting for an SM
-        ok = cudaStreamCreateWithFlags(&sl.s_gen, cudaStreamNonBlocking) == cudaSuccess &&
+        // blocks still waiting for an SM; so is the express slot's generation
+        ok = cudaStreamCreateWithPriority(&sl.s_gen, cudaStreamNonBlocking, i == kExpress ? prio_hi : prio_lo) ==
+                 cudaSuccess &&
              cudaHostAlloc(reinterpret_cast<void**>(&sl.h_units), nu * sizeof(vmt::UnitDesc), 0) == cudaSuccess &&
              cudaMalloc(reinterpret_cast<void**>(&sl.d_units), nu * sizeof(vmt::UnitDesc)) == cudaSuccess &&
              cudaHostAlloc(reinterpret_cast<void**>(&sl.h_map), nu * sizeof(int2), 0) == cudaSuccess &&
@@ -601,7 +653,7 @@ int vmt_server_release(vmt_server* s, uint64_t id)
             return VMT_EBUSY;
         }
         out = q.out;
-        if (q.admitted) s->used_out -= q.bytes;
+        if (q.admitted) (q.express ? s->used_out_express : s->used_out) -= q.bytes;
         s->reqs.erase(it);
     }
     if (out) cudaFreeAsync(out, s->s_free);
@@ -667,7 +719,7 @@ int vmt_server_stats(vmt_server* s, vmt_server_counters* out)
     out->failed = s->failed;
     out->bytes_out = s->bytes_out;
     out->state_bytes_in_use = s->used_state;
-    out->output_bytes_in_use = s->used_out;
+    out->output_bytes_in_use = s->used_out + s->used_out_express;
     out->peak_state_bytes = s->peak_state;
     out->peak_output_bytes = s->peak_out;
     out->host_launch_s = s->host_launch_s;

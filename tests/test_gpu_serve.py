@@ -170,11 +170,12 @@ def test_reserved_pool_and_counters(vmt):
 
 
 def test_cancel_queued_request(vmt):
-    # a small output budget keeps the later requests queued behind the first
+    # a small output budget keeps the later requests (too long for the express
+    # slot) queued behind the first
     srv = vmt.Server(state_budget=1 << 30, output_budget=(4 << 20) + 64, max_batch=16)
     a = srv.submit("mt32", 4, "u32", 1, 0, 1 << 20)     # 4 MiB: the whole budget
-    b = srv.submit("mt32", 4, "u32", 2, 0, 1000)
-    c = srv.submit("mt32", 4, "u32", 3, 0, 1000)
+    b = srv.submit("mt32", 4, "u32", 2, 0, 20000)
+    c = srv.submit("mt32", 4, "u32", 3, 0, 20000)
     srv.wait(a)
     assert srv.poll(c)[0] == vmt.SERVER_QUEUED            # a is not released yet
     srv.cancel(c)
@@ -186,7 +187,7 @@ def test_cancel_queued_request(vmt):
     assert ei.value.code == vmt.VMT_EBUSY
     srv.release(a)
     srv.wait(b)
-    assert np.array_equal(srv.copy(b, "u32"), _alone(vmt, "mt32", 4, "u32", 2, 0, 1000))
+    assert np.array_equal(srv.copy(b, "u32"), _alone(vmt, "mt32", 4, "u32", 2, 0, 20000))
     srv.release(b)
     srv.release(c)
     st = srv.stats()
@@ -255,5 +256,58 @@ def test_large_batch_uses_longer_chunks_and_stays_exact(vmt):
         srv.wait(rid)
         if k in (0, 5):                                    # full comparison for two of them
             assert np.array_equal(srv.copy(rid, "u32"), _alone(vmt, *c)), c
+        srv.release(rid)
+    srv.close()
+
+
+def test_small_requests_use_the_express_budget(vmt):
+    # a (4 MiB) is done but not released; b (8 MiB) then waits for the output
+    # budget (10 MiB).  Small requests go ahead of b on the express budget
+    # (10 MiB / 16 = 640 KiB) without taking output memory b waits for; once
+    # that budget is full the next small one queues like any other request.
+    srv = vmt.Server(state_budget=1 << 30, output_budget=10 << 20, max_batch=16)
+    a = srv.submit("mt32", 4, "u32", 1, 0, 1 << 20)
+    srv.wait(a)
+    b = srv.submit("mt32", 4, "u32", 2, 0, 2 << 20)
+    small = [srv.submit("mt32", 4, "u32", 3 + i, 0, 16384) for i in range(10)]   # 64 KiB each
+    for rid in small:
+        srv.wait(rid)
+    assert srv.poll(b)[0] == vmt.SERVER_QUEUED
+    st = srv.stats()
+    assert st["output_bytes_in_use"] == (4 << 20) + 10 * (64 << 10)
+    extra = srv.submit("mt32", 4, "u32", 99, 0, 1000)      # express budget full, main budget held by b
+    with pytest.raises(vmt.VMTError) as ei:
+        srv.wait(extra, timeout_ms=300)
+    assert ei.value.code == vmt.VMT_ETIMEOUT
+    srv.release(small[0])                                 # frees express room: extra goes ahead of b
+    srv.wait(extra)
+    assert srv.poll(b)[0] == vmt.SERVER_QUEUED
+    srv.release(a)
+    srv.wait(b)
+    assert np.array_equal(srv.copy(small[3], "u32"), _alone(vmt, "mt32", 4, "u32", 6, 0, 16384))
+    assert np.array_equal(srv.copy(extra, "u32"), _alone(vmt, "mt32", 4, "u32", 99, 0, 1000))
+    for rid in small[1:] + [b, extra]:
+        srv.release(rid)
+    assert srv.stats()["output_bytes_in_use"] == 0
+    srv.close()
+
+
+def test_small_request_goes_ahead_of_long_ones(vmt):
+    # one request per batch: four long requests (4 GiB each) take the four
+    # regular slots and a fifth waits for one of them; a small request
+    # submitted after it runs in the express slot and finishes first
+    srv = vmt.Server(state_budget=2 << 30, output_budget=32 << 30, max_batch=1)
+    n = (1 << 30) - 1
+    longs = [srv.submit("mt32", 16, "u32", 100 + i, 0, n) for i in range(5)]
+    small = srv.submit("sfmt", 8, "u32", 7, 3, 5000)
+    order = []
+    while len(order) < 6:
+        rid = srv.next_done(30_000_000)
+        assert rid is not None
+        assert srv.poll(rid)[0] == vmt.SERVER_DONE
+        order.append(rid)
+    assert order.index(small) < order.index(longs[4])
+    assert np.array_equal(srv.copy(small, "u32"), _alone(vmt, "sfmt", 8, "u32", 7, 3, 5000))
+    for rid in order:
         srv.release(rid)
     srv.close()
