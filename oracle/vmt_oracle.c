@@ -40,7 +40,8 @@
  *
  * Parity status: MT19937-32/64 recurrence, tempering and seeding are pinned by
  * library generators (Python's random, numpy, libstdc++) in the tests; the
- * jump is pinned by brute-force stepping and numpy's MT19937.jumped().
+ * jump is pinned by brute-force stepping, libstdc++'s discard(d) and the
+ * composition of jumps (jump(a) then jump(b) equals jump(a + b)).
  * SFMT19937: the recurrence is pinned algebraically (its minimal polynomial
  * must carry a primitive factor of degree 19937) and the certification by
  * its defining properties; SFMT seeding (the 32-bit initialisation over the
