@@ -441,13 +441,17 @@ int vmt_poly_x2pow(const uint64_t* mu, int64_t nw, int q_lo, int q_hi, uint64_t*
  *   - count * lanes of st must not exceed VMT_NOALLOC_MAX_LANE_STATES; larger
  *     states are rejected with VMT_EINVAL (nothing is enqueued);
  *   - the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture;
- *   - all calls share the one array: calls whose work overlaps on the GPU
- *     (different streams without ordering) race on it; order them on one
- *     stream or with events;
- *   - the caller's poly is read before the call returns (when nbits is not a
- *     multiple of 64 the call also waits for `cuda_stream`).
+ *     (cudaGetSymbolAddress) with that device current and keeps it with the
+ *     id of the device's CUDA context; make that first call before any stream
+ *     capture.  A call in a new context of the device (after cudaDeviceReset)
+ *     looks the address up again;
+ *   - all calls share the one array, which keeps the previous call's
+ *     contents: each call rewrites the polynomial row and the work items it
+ *     uses; calls whose work overlaps on the GPU (different streams without
+ *     ordering) race on it, so order them on one stream or with events;
+ *   - poly is read before the call returns, from any kind of host memory
+ *     (pageable or pinned): its words travel to the GPU as a kernel parameter,
+ *     so the call issues no copy and never waits for `cuda_stream`.
  */
 #define VMT_NOALLOC_MAX_LANE_STATES 16384
 int vmt_jump_noalloc(vmt_state* st, const uint64_t* poly, int64_t nbits, void* cuda_stream);

@@ -6,8 +6,11 @@ loops, plug-ins whose host forbids library allocations).  It must give exactly
 what vmt_jump gives.  Two identical generator sets are jumped, one with each
 entry point, twice in a row with different polynomials; the outputs generated
 after each jump must agree bit for bit (the tests' tolerance for integer
-output is zero).  The file is collected last and needs nothing from the other
-test files, so it passes alone in a fresh process and after the full suite.
+output is zero).  Further cases: a call at exactly the static limit of
+lane-states, one lane-state beyond it, and a polynomial in pinned host memory
+that the caller overwrites as soon as the call returns.  The file is collected
+last and needs nothing from the other test files, so it passes alone in a
+fresh process and after the full suite.
 """
 import ctypes
 
@@ -16,6 +19,8 @@ import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+LIMIT = 16384   # VMT_NOALLOC_MAX_LANE_STATES
 
 
 @pytest.fixture(scope="module")
@@ -35,12 +40,16 @@ def _u32(t):
     return t.cpu().view(torch.int32).numpy().view(np.uint32)
 
 
-def _noalloc_jump(vmt, g, poly, nbits):
-    poly = np.ascontiguousarray(poly, dtype=np.uint64)
+def _noalloc_jump_ptr(vmt, g, ptr, nbits):
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    rc = vmt.lib().vmt_jump_noalloc(g._h, ctypes.c_void_p(poly.ctypes.data), int(nbits), s)
+    rc = vmt.lib().vmt_jump_noalloc(g._h, ctypes.c_void_p(ptr), int(nbits), s)
     if rc != 0:
         raise vmt.VMTError(rc, vmt.lib().vmt_last_error().decode())
+
+
+def _noalloc_jump(vmt, g, poly, nbits):
+    poly = np.ascontiguousarray(poly, dtype=np.uint64)
+    _noalloc_jump_ptr(vmt, g, poly.ctypes.data, nbits)
 
 
 @pytest.mark.parametrize("variant,lanes", [("mt32", 16), ("sfmt", 4)])
@@ -60,6 +69,41 @@ def test_noalloc_jump_matches_jump_twice(vmt, variant, lanes):
         assert np.array_equal(ra, rb)
 
 
+def test_noalloc_at_the_limit_twice(vmt):
+    # 1024 generators x 16 lanes = exactly the largest accepted call: the last
+    # work item sits at the end of the static array
+    seeds = np.arange(7, 7 + 1024, dtype=np.uint64)
+    a = vmt.VGenerator("mt32", 16, seeds)
+    b = vmt.VGenerator("mt32", 16, seeds)
+    assert 1024 * 16 == LIMIT
+    for d in (987654321, 2**40 + 3):
+        p = vmt.jump_poly("mt32", d)
+        a.jump(p, p.size * 64)
+        _noalloc_jump(vmt, b, p, p.size * 64)
+        ra = _u32(a.generate(16 * 640, "u32"))
+        rb = _u32(b.generate(16 * 640, "u32"))
+        assert np.array_equal(ra, rb)
+
+
+def test_noalloc_pinned_poly_overwritten_after_the_call(vmt):
+    seeds = np.arange(100, 132, dtype=np.uint64)
+    a = vmt.VGenerator("mt64", 8, seeds)
+    b = vmt.VGenerator("mt64", 8, seeds)
+    p = vmt.jump_poly("mt64", 2**50 + 99)
+    pinned = torch.empty(p.size, dtype=torch.int64, pin_memory=True)
+    pinned.numpy().view(np.uint64)[:] = p
+    _ = a.generate(1 << 22, "u64")
+    a.jump(p, p.size * 64)
+    # queue work ahead of the call on the same stream, so that anything still
+    # reading the host buffer asynchronously would read it after the overwrite
+    _ = b.generate(1 << 22, "u64")
+    _noalloc_jump_ptr(vmt, b, pinned.data_ptr(), p.size * 64)
+    pinned.fill_(-1)                      # the caller reuses its buffer at once
+    ra = a.generate(8 * 1000, "u64").cpu().numpy()
+    rb = b.generate(8 * 1000, "u64").cpu().numpy()
+    assert np.array_equal(ra, rb)
+
+
 def test_noalloc_rejects_states_beyond_the_limit(vmt):
     g = vmt.VGenerator("mt32", 16, np.arange(1100, dtype=np.uint64))   # 17600 lane-states
     p = vmt.jump_poly("mt32", 5)
@@ -67,3 +111,7 @@ def test_noalloc_rejects_states_beyond_the_limit(vmt):
         _noalloc_jump(vmt, g, p, p.size * 64)
     assert ei.value.code == vmt.VMT_EINVAL
     assert "VMT_NOALLOC_MAX_LANE_STATES" in str(ei.value)
+    g1 = vmt.VGenerator("mt32", 1, np.arange(LIMIT + 1, dtype=np.uint64))   # one lane-state too many
+    with pytest.raises(vmt.VMTError) as ei:
+        _noalloc_jump(vmt, g1, p, p.size * 64)
+    assert ei.value.code == vmt.VMT_EINVAL
