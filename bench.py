@@ -36,6 +36,8 @@ from paper_2309_16682_gb300 import inputs as I  # noqa: E402
 
 METRIC = "random GB/s written (bit-exact)"
 UNIT = "GB/s"
+KERNELS = {"mt32": "gen_mt_kernel", "mt64": "gen_mt_kernel", "sfmt": "gen_sfmt_kernel"}
+ESIZE = {"u32": 4, "f32": 4, "u64": 8, "f64": 8}
 
 
 def profiled_traffic(key: str):
@@ -234,6 +236,18 @@ def oracle_sample_procs(workload: str, seconds: float, procs: int, steps: int = 
     return out
 
 
+def workload_config(workload: str, count: int, world: int, reduced: bool = False) -> dict:
+    """The `config` of a bench line: the same keys for both arms."""
+    w = I.WORKLOADS[workload]
+    segs = [(n // w["generators"], dt) for dt, n in w["outputs"]]
+    out_bytes = sum(n * count * ESIZE[dt] for n, dt in segs)
+    return {"workload": workload if not reduced else f"{workload}[:{count}]",
+            "variant": w["variant"], "lanes": w["lanes"],
+            "generators_per_gpu": count, "outputs_per_step": [[dt, n * count] for n, dt in segs],
+            "l2": "no flush: each step writes %.1f GiB (> 129 MB L2)" % (out_bytes / 2**30),
+            "parallelism": f"{world} independent GPU(s), generators sharded, no collective"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -257,7 +271,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "config": {"workload": args.workload},
+        "data": "synthetic", "config": workload_config(args.workload, w["generators"], 1),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -367,14 +381,116 @@ def run_served(vmt, requests: int, rate: float, plain_requests: int):
 # ---------------------------------------------------------------------------
 # GB300 arm
 # ---------------------------------------------------------------------------
+
+
+def kernel_key(workload: str) -> str:
+    w = I.WORKLOADS[workload]
+    return KERNELS[w["variant"]] + f"<{w['variant']}, M={w['lanes']}>"
+
+
+class Generation:
+    """One generation workload made resident on the GPU: its generators
+    (seeded and de-phased before any timing), its output buffers and the step
+    (one fused generate launch of all its output segments)."""
+
+    def __init__(self, vmt, workload: str, seeds, count: int):
+        import torch
+        self.vmt, self.workload = vmt, workload
+        w = I.WORKLOADS[workload]
+        self.w, self.count = w, count
+        self.segs = [(n // w["generators"], dt) for dt, n in w["outputs"]]   # outputs per generator
+        self.out_bytes = sum(n * count * ESIZE[dt] for n, dt in self.segs)
+        vmt.prepare(w["variant"])            # the variant's polynomial tables, untimed
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        self.g = vmt.VGenerator(w["variant"], w["lanes"], seeds)
+        torch.cuda.synchronize()
+        self.init_s = time.perf_counter() - t0
+        from paper_2309_16682_gb300 import UNITS
+        unit_bytes = {"mt32": 4, "mt64": 8, "sfmt": 16}[w["variant"]]
+        self.state_bytes = count * w["lanes"] * UNITS[vmt.VARIANTS[w["variant"]]] * unit_bytes
+        self.outs = [torch.empty((count, n), dtype=vmt._torch_dtype(dt), device="cuda") for n, dt in self.segs]
+
+    def step(self):
+        self.g.generate_multi(self.segs, outs=self.outs)
+
+    def time_steps(self, steps: int, warmup: int, world: int, clk=None):
+        """Warm-up, then `steps` timed steps between CUDA events on the
+        launching stream; returns (total ms over ranks, per-step ms)."""
+        import torch
+        stream = torch.cuda.current_stream()
+        for _ in range(max(warmup, 3)):
+            self.step()
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        if clk is not None:
+            clk.start()
+            time.sleep(0.3)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record(stream)
+        for k in range(steps):
+            self.step()
+            evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop() if clk is not None else None
+        barrier(world)
+        per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+        total_ms = max_over_ranks(world, evs[0].elapsed_time(evs[-1]))
+        return total_ms, per_step, clocks
+
+    def roofline(self, launch_ms: float, peak: float, peak_kind: str, write_peak: float):
+        alg = self.out_bytes + 2 * self.state_bytes
+        achieved = alg / (launch_ms / 1e3) / 1e9
+        out_gbs = self.out_bytes / (launch_ms / 1e3) / 1e9
+        t = profiled_traffic(kernel_key(self.workload))
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "write_peak": write_peak, "frac_of_write_peak": achieved / write_peak,
+                "traffic": t * self.count / self.w["generators"] if t is not None else None,
+                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg,
+                "output_only_frac": out_gbs / peak, "output_only_frac_of_write_peak": out_gbs / write_peak,
+                "kernel": kernel_key(self.workload)}
+
+    def close(self):
+        self.g.close()
+        self.outs = None
+
+
+def run_extra_config(vmt, workload: str, steps: int, warmup: int, world: int, rank: int, peak, peak_kind,
+                     write_peak):
+    """The other generation workloads, timed the same way as the headline
+    (every rank runs its own slice of the workload's generators)."""
+    from paper_2309_16682_gb300 import shard
+    w = I.WORKLOADS[workload]
+    count = w["generators"]
+    seeds = shard.rank_seeds(workload, world, rank, count)
+    job = Generation(vmt, workload, seeds, count)
+    total_ms, per_step, _ = job.time_steps(steps, warmup, world)
+    launch_ms = float(np.mean(per_step))
+    res = {"workload": workload, "variant": w["variant"], "lanes": w["lanes"], "generators_per_gpu": count,
+           "outputs_per_step": [[dt, n * count] for n, dt in job.segs], "steps": steps,
+           "ms_per_step": total_ms / steps, "value": job.out_bytes * steps * world / (total_ms / 1e3) / 1e9,
+           "unit": UNIT,
+           "words_per_s": sum(n * count for n, _ in job.segs) * steps * world / (total_ms / 1e3),
+           "step_ms": {"best": float(np.min(per_step)), "median": float(np.median(per_step))},
+           "init_s": job.init_s}
+    if count > 1:
+        res["roofline"] = job.roofline(launch_ms, peak, peak_kind, write_peak)
+        if job.out_bytes < (1 << 30):
+            res["l2"] = "outputs smaller than L2 stay partly cached"
+    else:
+        # one generator: a latency figure (one CTA does the whole call)
+        res["latency_us"] = 1e3 * float(np.median(per_step))
+        res["note"] = "one V-generator per call: latency-bound (a single CTA), not an HBM figure"
+    job.close()
+    return res
+
+
 def run_gb300(args, world, rank, local):
     import torch
     import paper_2309_16682_gb300 as vmt
     w = I.WORKLOADS[args.workload]
-    segs = [(n // w["generators"], dt) for dt, n in w["outputs"]]   # outputs per generator
     count = args.generators or w["generators"]
-    esize = {"u32": 4, "f32": 4, "u64": 8, "f64": 8}
-    out_bytes = sum(n * count * esize[dt] for n, dt in segs)
     # rank r owns generators [r * count, (r + 1) * count) of the workload's
     # global generator sequence (weak scaling, no collective on the data path)
     from paper_2309_16682_gb300 import shard
@@ -383,16 +499,9 @@ def run_gb300(args, world, rank, local):
 
     # one-time initialisation: seeding + jump-ahead de-phasing (timed
     # separately, after the variant's polynomial tables are built)
-    vmt.prepare(w["variant"])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    g = vmt.VGenerator(w["variant"], w["lanes"], seeds)
-    torch.cuda.synchronize()
-    init_s = time.perf_counter() - t0
-    from paper_2309_16682_gb300 import UNITS
-    unit_bytes = {"mt32": 4, "mt64": 8, "sfmt": 16}[w["variant"]]
-    state_bytes = count * w["lanes"] * UNITS[vmt.VARIANTS[w["variant"]]] * unit_bytes
-    outs = [torch.empty((count, n), dtype=vmt._torch_dtype(dt), device="cuda") for n, dt in segs]
+    job = Generation(vmt, args.workload, seeds, count)
+    g, segs, outs, out_bytes = job.g, job.segs, job.outs, job.out_bytes
+    init_s = job.init_s
     tuned = None
     if args.tune:
         # the autotuner times each compiled CTA size on this workload: its size
@@ -400,38 +509,16 @@ def run_gb300(args, world, rank, local):
         tuned = vmt.autotune(w["variant"], w["lanes"], count, 0, reps=3, segments=segs)
         vmt.tune_save(vmt.tune_cache_path())   # kept per GPU model; vmt.tune_load reapplies it
     tune_threads = vmt.tune_get(w["variant"], w["lanes"])
-    traffic_key = ("gen_sfmt_kernel" if w["variant"] == "sfmt" else "gen_mt_kernel") + f"<{w['variant']}, M={w['lanes']}>"
-
-    def step():
-        g.generate_multi(segs, outs=outs)
 
     # the HBM write ceiling of this GPU (store-only kernel), untimed
     write_peak = vmt.measure_store_bw(8 << 30, 5)
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    barrier(world)
-    torch.cuda.synchronize()
     clk = ClockSampler(local)
-    clk.start()
-    time.sleep(0.3)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    evs[0].record(stream)
-    for k in range(args.steps):
-        step()
-        evs[k + 1].record(stream)
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    barrier(world)
-    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    total_ms = max_over_ranks(world, total_ms)
+    total_ms, per_step, clocks = job.time_steps(args.steps, args.warmup, world, clk)
     value = out_bytes * args.steps * world / (total_ms / 1e3) / 1e9
     # the step is one kernel launch: its average duration is the step time
     launch_ms = float(np.mean(per_step))
-    alg_bytes = out_bytes + 2 * state_bytes
     peak, peak_kind = peaks()
-    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    roof = job.roofline(launch_ms, peak, peak_kind, write_peak)
 
     # end to end through the C ABI into pinned host memory
     e2e = None
@@ -458,7 +545,9 @@ def run_gb300(args, world, rank, local):
         e2e_val = out_bytes * e2e_steps * world / e2e_s / 1e9
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": out_bytes, "steps": e2e_steps,
-               "d2h_copy_gbs": copy_gbs, "frac_of_d2h_copy": e2e_val / world / copy_gbs}
+               "d2h_copy_gbs": copy_gbs, "frac_of_d2h_copy": e2e_val / world / copy_gbs,
+               "note": "vmt_generate_host into pinned host memory; the step has no host inputs (the generator "
+                       "states stay resident on the GPU between calls), so nothing is copied host to device"}
         del hosts
 
     # jump evaluation (a3) at full size: every lane of every generator by one
@@ -533,6 +622,20 @@ def run_gb300(args, world, rank, local):
                   "note": "vmt_scalar_drain: one u32 per query from a 16-lane MT32 V-generator, buffers of 2^22 "
                           "outputs refilled by the GPU while the host reads the other one"}
 
+    # the other generation workloads (MT19937-64 and SFMT19937 at full size,
+    # and the single 4-lane generator), timed like the headline
+    configs = None
+    if not args.no_configs:
+        g.close()
+        job.close()
+        outs = None
+        torch.cuda.empty_cache()
+        configs = {}
+        for name in [n for n in I.WORKLOADS if n != args.workload]:
+            configs[name] = run_extra_config(vmt, name, args.config_steps, args.warmup, world, rank, peak,
+                                             peak_kind, write_peak)
+            torch.cuda.empty_cache()
+
     served = None
     if not args.no_serve:
         served = run_served(vmt, args.serve_requests, 2.0e4, args.plain_requests)
@@ -557,27 +660,15 @@ def run_gb300(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": args.workload if not args.generators else f"{args.workload}[:{count}]",
-                       "variant": w["variant"], "lanes": w["lanes"],
-                       "generators_per_gpu": count, "outputs_per_step": [[dt, n * count] for n, dt in segs],
-                       "l2": "no flush: each step writes %.1f GiB (> 129 MB L2)" % (out_bytes / 2**30),
-                       "parallelism": f"{world} independent GPU(s), generators sharded, no collective"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "write_peak": write_peak, "frac_of_write_peak": achieved / write_peak,
-                         "traffic": (profiled_traffic(traffic_key) * count / w["generators"]
-                                     if profiled_traffic(traffic_key) is not None else None),
-                         "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": alg_bytes,
-                         "output_only_frac": out_bytes / (launch_ms / 1e3) / 1e9 / peak,
-                         "kernel": ("gen_sfmt_kernel" if w["variant"] == "sfmt" else "gen_mt_kernel") +
-                                   f"<{w['variant']}, M={w['lanes']}>"},
+            "config": workload_config(args.workload, count, world, args.generators),
+            "roofline": roof,
             "words_per_s": sum(n * count for n, _ in segs) * args.steps * world / (total_ms / 1e3),
             "step_ms": {"best": float(np.min(per_step)), "median": float(np.median(per_step)),
                         "mean": float(np.mean(per_step))},
             "gpu_launches": args.steps,
             "tuning": {"threads": tune_threads, "autotune": tuned},
             "e2e": e2e,
+            "configs": configs,
             "cpu_baseline": cpu,
             "init": {"seconds": init_s, "lane_jumps": lane_jumps, "lane_jumps_per_s": lane_jumps / init_s,
                      "note": "seed + jump-ahead de-phasing of all generators before the timed region (the "
@@ -609,6 +700,8 @@ def main():
     ap.add_argument("--generators", type=int, default=0,
                     help="smaller generator count (profiling cases); default: the workload's")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other generation workloads")
+    ap.add_argument("--config-steps", type=int, default=10, help="timed steps of each other generation workload")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
