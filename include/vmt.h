@@ -297,22 +297,53 @@ void* vmt_state_device_ptr(const vmt_state* st);
 int vmt_device_status(int reset);
 
 /*
- * Tuning of the generation kernels (the paper has no counterpart: CTA size is
- * a GPU-specific choice).  Each (variant, lanes) pair has a small set of
- * compiled CTA sizes; the table starts at the defaults, can be preset with the
- * environment variable VMT_TUNE="mt32:16:1024,mt64:8:512", set directly, or
- * filled by vmt_autotune, which times every compiled size on `count`
- * generators producing n_per_gen outputs of `dtype` (reps timed calls each,
- * after one warm-up) and keeps the fastest.  threads = 0 means the default.
+ * Tuning of the generation kernels (the paper has no counterpart: how a block
+ * of eq. (stepnomod) is spread over a CTA is a GPU-specific choice).  Each
+ * (variant, lanes) pair of MT19937-32/64 has a small list of compiled kernel
+ * configurations, described by vmt_tune_kernels as four ints each:
+ *   form           0: phase form -- one CTA per generator, every phase of
+ *                     n-m rows spread over all threads, a barrier between
+ *                     phases; 1: chain form -- a thread owns the rows j,
+ *                     j+(n-m), j+2(n-m) of one column (one barrier per block)
+ *   lanes_per_cta  lanes of the generator one CTA owns (chain form: M/lanes
+ *                     CTAs share a generator; unit launches use one CTA)
+ *   threads        CTA size
+ *   store_bytes    bytes per vector store (16 or 8)
+ * Entry 0 is the default.  Every configuration gives identical output.  The
+ * table starts at the defaults, can be preset with the environment variable
+ * VMT_TUNE="mt32:16:1024,mt64:8:#2" (a phase-form CTA size, or #index), set
+ * directly, or filled by the autotuner.
+ *   vmt_tune_set       select the phase-form configuration with `threads`
+ *                      threads (0: the default entry); VMT_EINVAL if none
+ *   vmt_tune_get       CTA size of the selected configuration
+ *   vmt_tune_kernels   writes min(count, cap) descriptions into desc
+ *                      (4 * cap ints) and returns count
+ *   vmt_tune_set_kernel / vmt_tune_get_kernel   select / read the index
+ *   vmt_autotune_grid  times every configuration on `count` generators
+ *                      producing the caller's segment list (as
+ *                      vmt_generate_multi: counts[i] outputs of dtypes[i] per
+ *                      generator), two alternating rounds of `reps` timed
+ *                      calls after a warm-up, each keeping its better mean;
+ *                      writes min(count, cap) times (ms per call) into ms_out,
+ *                      selects and returns the fastest in *best_index
+ *   vmt_autotune[_multi]   the same, returning the winner's CTA size and time
+ * SFMT19937 has one configuration.
  */
 int vmt_tune_set(int variant, int lanes, int threads);
 int vmt_tune_get(int variant, int lanes);
+int vmt_tune_kernels(int variant, int lanes, int* desc, int cap);
+int vmt_tune_set_kernel(int variant, int lanes, int index);
+int vmt_tune_get_kernel(int variant, int lanes);
+int vmt_autotune_grid(int variant, int lanes, int64_t count, int nseg, const int64_t* counts, const int* dtypes,
+                      int reps, void* cuda_stream, double* ms_out, int cap, int* best_index);
 /*
  * vmt_tune_save / vmt_tune_load -- the tuning table as a text file, one
- * "variant lanes threads" line per entry that differs from the default (the
- * autotuner's results can thus be kept per GPU model and reapplied).  load
- * applies every valid line and returns VMT_EINVAL if a line names a size that
- * is not compiled (the valid ones still apply) or the file cannot be read.
+ * "variant lanes form lanes_per_cta threads store_bytes" line per entry that
+ * differs from the default (the autotuner's results can thus be kept per GPU
+ * model and reapplied).  load also accepts "variant lanes threads" lines (a
+ * phase-form CTA size), applies every valid line and returns VMT_EINVAL if a
+ * line names a configuration that is not compiled (the valid ones still
+ * apply) or the file cannot be read.
  */
 int vmt_tune_save(const char* path);
 int vmt_tune_load(const char* path);
@@ -328,6 +359,17 @@ int vmt_tune_load(const char* path);
  */
 int vmt_tune_jump_set(int variant, int64_t split_below);
 int64_t vmt_tune_jump_get(int variant);
+/*
+ * vmt_tune_jump_compact -- on = 1: every jump launch of the variant (-1: all
+ * three) uses the compact CTA form: four warps per lane-jump over a ~20 KB
+ * ring of the sequence, extended in several rounds.  Each lane-jump is slower
+ * than in the sixteen-warp CTA form, but a CTA needs little shared memory, so
+ * it is scheduled next to long-running kernels of other streams (the server
+ * always uses this form for its initialisation).  on = 0 switches it off,
+ * on = -1 only reads.  Returns the setting before the call (1 or 0), or
+ * VMT_EINVAL for a bad variant.  Results are identical in every form.
+ */
+int vmt_tune_jump_compact(int variant, int on);
 
 /*
  * vmt_stream_generate -- exact single-stream mode: the first n outputs, from
@@ -424,6 +466,48 @@ int vmt_set_cache_dir(const char* path);
 int vmt_poly_minpoly(const uint64_t* bits, int64_t n, uint64_t* mu_out, int64_t cap_words);
 int vmt_poly_mulmod(const uint64_t* a, const uint64_t* b, const uint64_t* mu, uint64_t* out, int64_t nw);
 int vmt_poly_x2pow(const uint64_t* mu, int64_t nw, int q_lo, int q_hi, uint64_t* out);
+
+/*
+ * Twisted GFSR generators with run-time parameters (Sec. 2.1 eq. step with
+ * other constants; Sec. 3.1 jump; the paper's future-work remark that the
+ * construction applies to other F2-linear generators).  A state is n
+ * uint32 words on the device, x_k .. x_{k+n-1} oldest first, each holding a
+ * w-bit word.  The recurrence is
+ *     x_{k+n} = x_{k+m} xor (y >> 1) xor (y odd ? a : 0),
+ *     y = (upper w-r bits of x_k) | (lower r bits of x_{k+1}),
+ * and an output is x_{k+n}, or with temper != 0 the tempering of eq.
+ * (tempering) with shifts u, s, t, l and masks d, b, c, truncated to w bits.
+ * Compiled state sizes: n = 4, 5 or 17 (VMT_EINVAL otherwise); 2 <= w <= 32,
+ * 1 <= m < n, 1 <= r < w, a < 2^w.
+ */
+typedef struct vmt_tgfsr {
+    int w, n, m, r;
+    uint32_t a;
+    int temper;
+    int u, s, t, l;
+    uint32_t d, b, c;
+} vmt_tgfsr;
+/*
+ * vmt_tgfsr_jump -- replace each of `count` states (states: count x n words,
+ * device) by c(F) X, c the polynomial of nbits bits in poly (host, bit i of
+ * poly[i/64] = coefficient of x^i, copied before the call returns).  Runs the
+ * window-correlation jump kernels of vmt_jump: kernel 0 one warp per state,
+ * 1 one CTA per state.  With c = x^J mod the minimal polynomial of the
+ * transition (vmt_poly_minpoly on output bits, then vmt_poly_x2pow /
+ * vmt_poly_mulmod) this advances every state by J steps.  Allocates its
+ * scratch from the stream-ordered pool.  Asynchronous on cuda_stream.
+ */
+int vmt_tgfsr_jump(const vmt_tgfsr* g, int64_t count, void* states, const uint64_t* poly, int64_t nbits, int kernel,
+                   void* cuda_stream);
+/*
+ * vmt_tgfsr_generate -- `count` = G * lanes states advance n steps each;
+ * output word k of lane t of group g is stored at out[(g * n + k) * lanes + t]
+ * (device, uint32: the interleaved stream of eq. combseq for a V-generator
+ * of `lanes` lanes), and the advanced states are written back, so calls
+ * continue the streams.  Asynchronous on cuda_stream.
+ */
+int vmt_tgfsr_generate(const vmt_tgfsr* g, int64_t count, int lanes, void* states, int64_t n, void* out,
+                       void* cuda_stream);
 
 /*
  * vmt_jump_noalloc -- vmt_jump for callers that cannot allocate device memory.

@@ -106,6 +106,13 @@ def lib() -> ctypes.CDLL:
             "vmt_tune_jump_get": (I64, [I]),
             "vmt_autotune": (I, [I, I, I64, I64, I, I, P, P, P]),
             "vmt_autotune_multi": (I, [I, I, I64, I, P, P, I, P, P, P]),
+            "vmt_tune_kernels": (I, [I, I, P, I]),
+            "vmt_tune_jump_compact": (I, [I, I]),
+            "vmt_tgfsr_jump": (I, [P, I64, P, P, I64, I, P]),
+            "vmt_tgfsr_generate": (I, [P, I64, I, P, I64, P, P]),
+            "vmt_tune_set_kernel": (I, [I, I, I]),
+            "vmt_tune_get_kernel": (I, [I, I]),
+            "vmt_autotune_grid": (I, [I, I, I64, I, P, P, I, P, P, I, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -385,6 +392,42 @@ def tune_jump(variant: str, split_below: int | None = None) -> int:
     return old
 
 
+def tune_jump_compact(variant: str, on: bool | None = None) -> bool:
+    """Every jump launch of the variant in the compact CTA form (on=True), or
+    the default choice (False); returns the setting before the call (None:
+    just read)."""
+    return bool(_check(lib().vmt_tune_jump_compact(VARIANTS[variant], -1 if on is None else int(bool(on)))))
+
+
+class Tgfsr(ctypes.Structure):
+    """Parameters of a twisted GFSR with run-time constants (vmt_tgfsr)."""
+    _fields_ = [("w", ctypes.c_int), ("n", ctypes.c_int), ("m", ctypes.c_int), ("r", ctypes.c_int),
+                ("a", ctypes.c_uint32), ("temper", ctypes.c_int), ("u", ctypes.c_int), ("s", ctypes.c_int),
+                ("t", ctypes.c_int), ("l", ctypes.c_int), ("d", ctypes.c_uint32), ("b", ctypes.c_uint32),
+                ("c", ctypes.c_uint32)]
+
+
+def tgfsr_jump(params: Tgfsr, states, poly: np.ndarray, nbits: int | None = None, kernel: str = "warp",
+               stream=None) -> None:
+    """Every state (a uint32 tensor [count, n] on the GPU) by c(F) X (Sec. 3.1)."""
+    poly = np.ascontiguousarray(poly, dtype=np.uint64)
+    nb = poly.size * 64 if nbits is None else int(nbits)
+    _check(lib().vmt_tgfsr_jump(ctypes.byref(params), int(states.shape[0]), ctypes.c_void_p(states.data_ptr()),
+                                _np_ptr(poly), nb, {"warp": 0, "cta": 1}[kernel], _stream_handle(stream)))
+
+
+def tgfsr_generate(params: Tgfsr, states, lanes: int, n: int, out=None, stream=None):
+    """n outputs of every state, interleaved over `lanes` (tensor [groups, n * lanes])."""
+    import torch
+    groups = int(states.shape[0]) // int(lanes)
+    if out is None:
+        out = torch.empty((groups, n * lanes), dtype=torch.int32, device=states.device)   # uint32 words
+    _check(lib().vmt_tgfsr_generate(ctypes.byref(params), int(states.shape[0]), int(lanes),
+                                    ctypes.c_void_p(states.data_ptr()), int(n), ctypes.c_void_p(out.data_ptr()),
+                                    _stream_handle(stream)))
+    return out
+
+
 def tune_save(path: str) -> None:
     """Write the tuning table (entries that differ from the defaults)."""
     _check(lib().vmt_tune_save(os.fspath(path).encode()))
@@ -405,6 +448,41 @@ def tune_cache_path() -> str:
 
 def tune_get(variant: str, lanes: int) -> int:
     return _check(lib().vmt_tune_get(VARIANTS[variant], int(lanes)))
+
+
+FORMS = {0: "phase", 1: "chain"}
+
+
+def tune_kernels(variant: str, lanes: int) -> list[dict]:
+    """The compiled generation-kernel configurations of (variant, lanes), in
+    index order (entry 0 is the default)."""
+    n = _check(lib().vmt_tune_kernels(VARIANTS[variant], int(lanes), None, 0))
+    buf = (ctypes.c_int * max(1, 4 * n))()
+    _check(lib().vmt_tune_kernels(VARIANTS[variant], int(lanes), buf, n))
+    return [{"form": FORMS[buf[4 * i]], "lanes_per_cta": buf[4 * i + 1], "threads": buf[4 * i + 2],
+             "store_bytes": buf[4 * i + 3]} for i in range(n)]
+
+
+def tune_set_kernel(variant: str, lanes: int, index: int) -> None:
+    _check(lib().vmt_tune_set_kernel(VARIANTS[variant], int(lanes), int(index)))
+
+
+def tune_get_kernel(variant: str, lanes: int) -> int:
+    return _check(lib().vmt_tune_get_kernel(VARIANTS[variant], int(lanes)))
+
+
+def autotune_grid(variant: str, lanes: int, count: int, segments, reps: int = 3, stream=None):
+    """Time every compiled configuration of (variant, lanes) on `count`
+    generators producing `segments` [(n per generator, dtype), ...]; selects
+    the fastest.  Returns (best index, [ms per call of each configuration])."""
+    cands = tune_kernels(variant, lanes)
+    ms = (ctypes.c_double * max(1, len(cands)))()
+    best = ctypes.c_int(0)
+    counts = (ctypes.c_int64 * len(segments))(*[int(n) for n, _ in segments])
+    dts = (ctypes.c_int * len(segments))(*[DTYPES[d] for _, d in segments])
+    _check(lib().vmt_autotune_grid(VARIANTS[variant], int(lanes), int(count), len(segments), counts, dts, int(reps),
+                                   _stream_handle(stream), ms, len(cands), ctypes.byref(best)))
+    return best.value, [float(ms[i]) for i in range(len(cands))]
 
 
 def autotune(variant: str, lanes: int, count: int, n_per_gen: int, dtype: str = "u32", reps: int = 3, stream=None,

@@ -39,6 +39,71 @@ struct UnitDesc {
     char* out;           // first output element
 };
 
+// Compiled configurations of the MT generation kernels, per (variant, lanes);
+// the first row of a pair is its default.  form: kPhase = one CTA per
+// generator, all threads on each phase of eq. (stepnomod), a barrier between
+// phases (gen_mt.cu); kChain = a thread owns a chain of rows j, j+(n-m),
+// j+2(n-m), one barrier per block, a CTA owns lpc of the M lanes (gen_mtc*.cu).
+// store = bytes per vector store (16 or 8).
+enum { kPhase = 0, kChain = 1 };
+struct KernelCfg {
+    int variant, lanes, form, lpc, threads, store;
+};
+constexpr KernelCfg kKernelCfgs[] = {
+    // V-MT19937-32
+    {VMT_MT19937_32, 16, kPhase, 16, 512, 16},
+    {VMT_MT19937_32, 16, kPhase, 16, 1024, 16},
+    {VMT_MT19937_32, 16, kChain, 8, 256, 16},
+    {VMT_MT19937_32, 16, kChain, 16, 512, 16},
+    {VMT_MT19937_32, 16, kChain, 8, 128, 16},
+    {VMT_MT19937_32, 16, kChain, 8, 256, 8},
+    {VMT_MT19937_32, 8, kPhase, 8, 256, 16},
+    {VMT_MT19937_32, 8, kPhase, 8, 512, 16},
+    {VMT_MT19937_32, 8, kChain, 8, 256, 16},
+    {VMT_MT19937_32, 8, kChain, 8, 128, 16},
+    {VMT_MT19937_32, 4, kPhase, 4, 256, 16},
+    {VMT_MT19937_32, 4, kChain, 4, 128, 16},
+    // V-MT19937-64
+    {VMT_MT19937_64, 16, kPhase, 16, 512, 16},
+    {VMT_MT19937_64, 16, kPhase, 16, 1024, 16},
+    {VMT_MT19937_64, 16, kChain, 4, 160, 16},
+    {VMT_MT19937_64, 16, kChain, 8, 320, 16},
+    {VMT_MT19937_64, 8, kPhase, 8, 256, 16},
+    {VMT_MT19937_64, 8, kPhase, 8, 512, 16},
+    {VMT_MT19937_64, 8, kChain, 4, 160, 16},
+    {VMT_MT19937_64, 8, kChain, 8, 320, 16},
+    {VMT_MT19937_64, 8, kChain, 4, 160, 8},
+    {VMT_MT19937_64, 4, kPhase, 4, 256, 16},
+    {VMT_MT19937_64, 4, kChain, 4, 160, 16},
+};
+constexpr int kNumKernelCfgs = static_cast<int>(sizeof(kKernelCfgs) / sizeof(kKernelCfgs[0]));
+
+// row of the table for candidate `index` of (variant, lanes), or nullptr
+inline const KernelCfg* kernel_cfg(int variant, int lanes, int index)
+{
+    int k = 0;
+    for (int i = 0; i < kNumKernelCfgs; ++i)
+        if (kKernelCfgs[i].variant == variant && kKernelCfgs[i].lanes == lanes) {
+            if (k == index) return &kKernelCfgs[i];
+            ++k;
+        }
+    return nullptr;
+}
+
+inline int kernel_cfg_count(int variant, int lanes)
+{
+    int k = 0;
+    for (int i = 0; i < kNumKernelCfgs; ++i) k += kKernelCfgs[i].variant == variant && kKernelCfgs[i].lanes == lanes;
+    return k;
+}
+
+// Multipliers 2^s for the left shifts of the tempering (see vmt_device.cuh):
+// kernel parameters, set by every launch of the MT generation kernels.
+struct ShiftK {
+    uint32_t p7, p15, p17, p5;
+};
+constexpr ShiftK kShiftK{1u << 7, 1u << 15, 1u << 17, 1u << 5};
+
 struct GenArgs {
     void* states;      // [gens][block words] (lock-step mode)
     long long gens;    // generators (lock-step) or units (unit mode) in the launch
@@ -48,9 +113,12 @@ struct GenArgs {
     long long total;   // native words per generator in this call (lock-step mode)
     int nseg;
     SegArg seg[VMT_MAXSEG];
-    int threads;       // CTA size among the compiled ones (0: default), set by the tuning table
+    int kcfg;          // kernel configuration: candidate index of (variant, lanes) in kKernelCfgs (0: default)
     const UnitDesc* units;   // unit mode when non-null: one entry per unit, longest first
     int* work_counter;       // unit mode: next unit = atomicAdd(work_counter, 1) (zeroed before launch)
+    ShiftK k;                // tempering multipliers (set by the MT launchers)
+    int cta_per_unit;        // unit mode: one CTA per unit instead of a persistent grid, so that CTAs of
+                             // other (higher-priority) streams get an SM whenever a unit finishes
 };
 
 }  // namespace vmt

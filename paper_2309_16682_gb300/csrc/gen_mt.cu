@@ -15,311 +15,16 @@
 // Within a phase, row k also reads the old x_{k+1} that row k+1 overwrites, so
 // each phase loads all operands, synchronises, then writes.
 #include "bulk.cuh"
-#include "vmt_device.cuh"
+#include "gen_mt.cuh"
 
 namespace vmt {
 namespace dev {
-
-template <typename W, int VW> struct VecOf;
-template <> struct VecOf<uint32_t, 4> { using T = uint4; };
-template <> struct VecOf<uint32_t, 2> { using T = uint2; };
-template <> struct VecOf<uint32_t, 1> { using T = uint32_t; };
-template <> struct VecOf<unsigned long long, 2> { using T = ulonglong2; };
-template <> struct VecOf<unsigned long long, 1> { using T = unsigned long long; };
-
-template <typename W, int VW>
-__device__ __forceinline__ void ldv(const W* p, W (&w)[VW])
-{
-    using T = typename VecOf<W, VW>::T;
-    const T t = *reinterpret_cast<const T*>(p);
-    memcpy(w, &t, sizeof(T));
-}
-
-template <typename W, int VW>
-__device__ __forceinline__ void stv(W* p, const W (&w)[VW])
-{
-    using T = typename VecOf<W, VW>::T;
-    T t;
-    memcpy(&t, w, sizeof(T));
-    *reinterpret_cast<T*>(p) = t;
-}
-
-template <int VW>
-__device__ __forceinline__ void emit_words(const Emitter& em, long long f0, const uint32_t (&z)[VW], long long lo,
-                                           long long hi, long long ebase)
-{
-    em.emit32<VW>(f0, z, lo, hi, ebase);
-}
-
-template <int VW>
-__device__ __forceinline__ void emit_words(const Emitter& em, long long f0, const unsigned long long (&z)[VW],
-                                           long long lo, long long hi, long long ebase)
-{
-    em.emit64<VW>(f0, z, lo, hi, ebase);
-}
-
-// Bytes of output per native word for an output type: 32-bit words give 4
-// (u32, f32, and u64/f64 built from two words); 64-bit words give 8 (u64,
-// f64) or 4 (f32).
-template <typename W>
-__device__ __forceinline__ int bytes_per_word(int dt)
-{
-    return (sizeof(W) == 4 || dt == VMT_F32) ? 4 : 8;
-}
-
-// Output plan of one block, spread over the lanes of every warp: lane s holds
-// segment s (base address such that block word f goes to base + f * bpw, and
-// its output type); every lane holds the block-coordinate segment boundaries.
-// A 16-byte vector at block word f0 then needs three compares and two shuffles
-// to find its segment and address.
-struct BlockPlan {
-    long long my_base;
-    int my_dt;
-    int b1, b2, b3;
-    bool fast;   // every segment base aligned to a vector and every boundary on a vector
-
-    template <class P, typename W, int VW>
-    __device__ __forceinline__ void make(const GenArgs& a, const Emitter& em, long long delta)
-    {
-        const int lane = threadIdx.x & 31;
-        int bnd = 0x7FFFFFFF;
-        bool ok = true;
-        my_base = 0;
-        my_dt = VMT_U32;
-        if (lane < a.nseg) {
-            const SegArg& sg = a.seg[lane];
-            const int bpw = bytes_per_word<W>(sg.dtype);
-            const int esz = (sg.dtype == VMT_U32 || sg.dtype == VMT_F32) ? 4 : 8;
-            my_dt = sg.dtype;
-            (void)esz;
-            my_base = reinterpret_cast<long long>(em.elem0(lane)) + (delta - sg.wbeg) * bpw;
-            ok = (my_base % (VW * bpw)) == 0;
-            long long b = sg.wbeg - delta;   // block word where the segment starts
-            if (b < -1) b = -1;
-            if (b > (1LL << 30)) b = 1LL << 30;
-            bnd = static_cast<int>(b);
-            if (b > 0 && b < (1LL << 30) && (b % VW) != 0) ok = false;
-        }
-        fast = __all_sync(0xFFFFFFFFu, ok);
-        b1 = __shfl_sync(0xFFFFFFFFu, bnd, 1);
-        b2 = __shfl_sync(0xFFFFFFFFu, bnd, 2);
-        b3 = __shfl_sync(0xFFFFFFFFu, bnd, 3);
-        if (a.nseg < 2) b1 = 0x7FFFFFFF;
-        if (a.nseg < 3) b2 = 0x7FFFFFFF;
-        if (a.nseg < 4) b3 = 0x7FFFFFFF;
-    }
-};
-
-// store VW tempered words at block word f0 (fast path; the whole vector is in
-// range, in one segment and aligned).  Executed by all lanes of the warp (the
-// shuffles need them); `doit` masks the store.
-template <typename W, int VW>
-__device__ __forceinline__ void plan_store(const BlockPlan& P, int f0, const W (&z)[VW], bool doit)
-{
-    const int s = (f0 >= P.b1) + (f0 >= P.b2) + (f0 >= P.b3);
-    const long long base = __shfl_sync(0xFFFFFFFFu, P.my_base, s);
-    const int dt = __shfl_sync(0xFFFFFFFFu, P.my_dt, s);
-    if (!doit) return;
-    if (sizeof(W) == 4) {
-        const uint32_t* u = reinterpret_cast<const uint32_t*>(z);
-        char* ptr = reinterpret_cast<char*>(base + 4LL * f0);
-        if (VW == 4) {
-            if (dt == VMT_U32) __stcs(reinterpret_cast<uint4*>(ptr), make_uint4(u[0], u[1 % VW], u[2 % VW], u[3 % VW]));
-            else if (dt == VMT_F32)
-                __stcs(reinterpret_cast<float4*>(ptr), make_float4(f32_of_u32(u[0]), f32_of_u32(u[1 % VW]),
-                                                                   f32_of_u32(u[2 % VW]), f32_of_u32(u[3 % VW])));
-            else if (dt == VMT_U64) {
-                ulonglong2 v;
-                v.x = static_cast<unsigned long long>(u[0]) | (static_cast<unsigned long long>(u[1 % VW]) << 32);
-                v.y = static_cast<unsigned long long>(u[2 % VW]) | (static_cast<unsigned long long>(u[3 % VW]) << 32);
-                __stcs(reinterpret_cast<ulonglong2*>(ptr), v);
-            } else {
-                double2 v;
-                v.x = f64_of_pair(u[0], u[1 % VW]);
-                v.y = f64_of_pair(u[2 % VW], u[3 % VW]);
-                __stcs(reinterpret_cast<double2*>(ptr), v);
-            }
-        } else if (VW == 2) {
-            if (dt == VMT_U32) __stcs(reinterpret_cast<uint2*>(ptr), make_uint2(u[0], u[1 % VW]));
-            else if (dt == VMT_F32) __stcs(reinterpret_cast<float2*>(ptr), make_float2(f32_of_u32(u[0]), f32_of_u32(u[1 % VW])));
-            else if (dt == VMT_U64)
-                __stcs(reinterpret_cast<unsigned long long*>(ptr),
-                       static_cast<unsigned long long>(u[0]) | (static_cast<unsigned long long>(u[1 % VW]) << 32));
-            else __stcs(reinterpret_cast<double*>(ptr), f64_of_pair(u[0], u[1 % VW]));
-        } else {
-            if (dt == VMT_U32) __stcs(reinterpret_cast<uint32_t*>(ptr), u[0]);
-            else if (dt == VMT_F32) __stcs(reinterpret_cast<float*>(ptr), f32_of_u32(u[0]));
-        }
-    } else {
-        const unsigned long long* u = reinterpret_cast<const unsigned long long*>(z);
-        if (dt == VMT_F32) {
-            char* ptr = reinterpret_cast<char*>(base + 4LL * f0);
-            if (VW == 2) __stcs(reinterpret_cast<float2*>(ptr), make_float2(f32_of_u64(u[0]), f32_of_u64(u[1 % VW])));
-            else __stcs(reinterpret_cast<float*>(ptr), f32_of_u64(u[0]));
-        } else {
-            char* ptr = reinterpret_cast<char*>(base + 8LL * f0);
-            if (VW == 2) {
-                if (dt == VMT_U64) {
-                    ulonglong2 v;
-                    v.x = u[0];
-                    v.y = u[1 % VW];
-                    __stcs(reinterpret_cast<ulonglong2*>(ptr), v);
-                } else {
-                    double2 v;
-                    v.x = f64_of_u64(u[0]);
-                    v.y = f64_of_u64(u[1 % VW]);
-                    __stcs(reinterpret_cast<double2*>(ptr), v);
-                }
-            } else {
-                if (dt == VMT_U64) __stcs(reinterpret_cast<unsigned long long*>(ptr), u[0]);
-                else __stcs(reinterpret_cast<double*>(ptr), f64_of_u64(u[0]));
-            }
-        }
-    }
-}
-
-// Emit the vector of VW tempered words at block word f0 whose valid block
-// range is [lo, hi); delta converts block words to call words.
-template <typename W, int VW>
-__device__ __forceinline__ void emit_vec(const BlockPlan& P, const Emitter& em, int f0, const W (&z)[VW], int lo,
-                                         int hi, long long delta, bool active)
-{
-    const bool full = active && f0 >= lo && f0 + VW <= hi;
-    if (P.fast) {
-        plan_store<W, VW>(P, f0, z, full);
-        if (full || !active) return;
-    }
-    if (active) emit_words<VW>(em, f0, z, lo, hi, delta + lo);
-}
-
-// Output policy: the output types of a call known at compile time (one
-// segment, or two segments split at a run-time boundary), or GENERIC (any
-// segment list, resolved per vector through BlockPlan).
-template <int DT0_, int DT1_>
-struct Pol {
-    static constexpr int DT0 = DT0_, DT1 = DT1_;
-    static constexpr bool generic = DT0_ < 0;
-    static constexpr int nseg = generic ? 0 : (DT1_ < 0 ? 1 : 2);
-};
-using PolGeneric = Pol<-1, -1>;
-
-// store VW words of one statically typed segment at base + f0 * bytes_per_word
-template <int DT, typename W, int VW>
-__device__ __forceinline__ void store_typed(long long base, int f0, const W (&z)[VW])
-{
-    if constexpr (sizeof(W) == 4) {
-        const uint32_t* u = reinterpret_cast<const uint32_t*>(z);
-        char* ptr = reinterpret_cast<char*>(base + 4LL * f0);
-        if constexpr (VW == 4) {
-            if constexpr (DT == VMT_U32) __stcs(reinterpret_cast<uint4*>(ptr), make_uint4(u[0], u[1], u[2], u[3]));
-            if constexpr (DT == VMT_F32)
-                __stcs(reinterpret_cast<float4*>(ptr),
-                       make_float4(f32_of_u32(u[0]), f32_of_u32(u[1]), f32_of_u32(u[2]), f32_of_u32(u[3])));
-            if constexpr (DT == VMT_U64) {
-                ulonglong2 v;
-                v.x = static_cast<unsigned long long>(u[0]) | (static_cast<unsigned long long>(u[1]) << 32);
-                v.y = static_cast<unsigned long long>(u[2]) | (static_cast<unsigned long long>(u[3]) << 32);
-                __stcs(reinterpret_cast<ulonglong2*>(ptr), v);
-            }
-            if constexpr (DT == VMT_F64) {
-                double2 v;
-                v.x = f64_of_pair(u[0], u[1]);
-                v.y = f64_of_pair(u[2], u[3]);
-                __stcs(reinterpret_cast<double2*>(ptr), v);
-            }
-        }
-    } else {
-        const unsigned long long* u = reinterpret_cast<const unsigned long long*>(z);
-        if constexpr (VW == 2) {
-            if constexpr (DT == VMT_F32)
-                __stcs(reinterpret_cast<float2*>(reinterpret_cast<char*>(base + 4LL * f0)),
-                       make_float2(f32_of_u64(u[0]), f32_of_u64(u[1])));
-            if constexpr (DT == VMT_U64) {
-                ulonglong2 v;
-                v.x = u[0];
-                v.y = u[1];
-                __stcs(reinterpret_cast<ulonglong2*>(reinterpret_cast<char*>(base + 8LL * f0)), v);
-            }
-            if constexpr (DT == VMT_F64) {
-                double2 v;
-                v.x = f64_of_u64(u[0]);
-                v.y = f64_of_u64(u[1]);
-                __stcs(reinterpret_cast<double2*>(reinterpret_cast<char*>(base + 8LL * f0)), v);
-            }
-        }
-    }
-}
-
-// Per-block plan for a static policy: segment bases and the boundary in block
-// words; ok when both bases are vector-aligned and the boundary falls on a vector.
-struct TypedPlan {
-    long long base0, base1;
-    int b1;
-    bool ok;
-
-    template <class P, typename W, int VW>
-    __device__ __forceinline__ void make(const GenArgs& a, const Emitter& em, long long delta)
-    {
-        const int bpw0 = bytes_per_word<W>(P::DT0);
-        const int esz0 = (P::DT0 == VMT_U32 || P::DT0 == VMT_F32) ? 4 : 8;
-        (void)esz0;
-        base0 = reinterpret_cast<long long>(em.elem0(0)) + (delta - a.seg[0].wbeg) * bpw0;
-        ok = (base0 % (VW * bpw0)) == 0;
-        b1 = 0x7FFFFFFF;
-        base1 = 0;
-        if constexpr (P::nseg == 2) {
-            const int bpw1 = bytes_per_word<W>(P::DT1);
-            const int esz1 = (P::DT1 == VMT_U32 || P::DT1 == VMT_F32) ? 4 : 8;
-            (void)esz1;
-            base1 = reinterpret_cast<long long>(em.elem0(1)) + (delta - a.seg[1].wbeg) * bpw1;
-            ok = ok && (base1 % (VW * bpw1)) == 0;
-            long long b = a.seg[1].wbeg - delta;
-            if (b < -1) b = -1;
-            if (b > (1LL << 30)) b = 1LL << 30;
-            b1 = static_cast<int>(b);
-            if (b > 0 && b < (1LL << 30) && (b % VW) != 0) ok = false;
-        }
-    }
-};
-
-template <class P>
-struct PlanOf {
-    using type = TypedPlan;
-};
-template <>
-struct PlanOf<PolGeneric> {
-    using type = BlockPlan;
-};
-
-// Emit the vector at block word f0 (valid block range [lo, hi); block word f
-// is call word f + delta).  `check` is false when the whole vector is known to
-// be in range.  All lanes call this (the generic plan shuffles).
-template <class P, typename W, int VW>
-__device__ __forceinline__ void emit_p(const typename PlanOf<P>::type& plan, const Emitter& em, int f0,
-                                       const W (&z)[VW], int lo, int hi, long long delta, bool active, bool check)
-{
-    const bool full = active && (!check || (f0 >= lo && f0 + VW <= hi));
-    if constexpr (P::generic) {
-        if (plan.fast) {
-            plan_store<W, VW>(plan, f0, z, full);
-            if (full || !active) return;
-        }
-        if (active) emit_words<VW>(em, f0, z, lo, hi, delta + lo);
-    } else {
-        if (full && plan.ok) {
-            if (P::nseg == 1 || f0 < plan.b1) store_typed<P::DT0, W, VW>(plan.base0, f0, z);
-            else store_typed<(P::nseg == 2 ? P::DT1 : P::DT0), W, VW>(plan.base1, f0, z);
-        } else if (active) {
-            emit_words<VW>(em, f0, z, lo, hi, delta + lo);
-        }
-    }
-}
 
 // One item of a twist phase: vector v of the new block from the old block
 // `cur` and the rows of `nxt` finished by earlier phases.
 template <class G, int M, int VW, int K0, int K1>
 __device__ __forceinline__ void twist_item(const typename G::W* cur, typename G::W* nxt, int v,
-                                           typename G::W (&z)[VW])
+                                           typename G::W (&z)[VW], const ShiftK& k)
 {
     using W = typename G::W;
     constexpr int N = G::N, MM = G::MM, NM = N - MM;
@@ -332,8 +37,8 @@ __device__ __forceinline__ void twist_item(const typename G::W* cur, typename G:
     else ldv<W, VW>(nxt + (v - NM * RV) * VW, xc);                  // new x_{k-(n-m)}
 #pragma unroll
     for (int u = 0; u < VW; ++u) {
-        nw[u] = G::twist(xa[u], xb[u], xc[u]);
-        z[u] = G::temper(nw[u]);
+        nw[u] = G::twist(xa[u], xb[u], xc[u], k);
+        z[u] = G::temper(nw[u], k);
     }
     stv<W, VW>(nxt + v * VW, nw);
 }
@@ -361,7 +66,7 @@ __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G
                 const int v = V0 + tid + i * T;
                 if (((i + 1) * T <= V1 - V0) || v < V1) {
                     W z[VW];
-                    twist_item<G, M, VW, K0, K1>(cur, nxt, v, z);
+                    twist_item<G, M, VW, K0, K1>(cur, nxt, v, z, em.a.k);
                     if (P::nseg == 2 && second) store_typed<(P::nseg == 2 ? P::DT1 : P::DT0), W, VW>(base, v * VW, z);
                     else store_typed<P::DT0, W, VW>(base, v * VW, z);
                 }
@@ -374,7 +79,7 @@ __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G
         const int v = V0 + tid + i * T;
         const bool act = ((i + 1) * T <= V1 - V0) || v < V1;   // static for all but the last item
         W z[VW];
-        if (act) twist_item<G, M, VW, K0, K1>(cur, nxt, v, z);
+        if (act) twist_item<G, M, VW, K0, K1>(cur, nxt, v, z, em.a.k);
         else {
 #pragma unroll
             for (int u = 0; u < VW; ++u) z[u] = W(0);
@@ -386,16 +91,19 @@ __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G
 // set by a kernel whose bounded wait on a bulk copy gave up
 __device__ int g_gen_timeout = 0;
 
-// CTAs that fit on one SM: by threads (2048) and by shared memory (two copies
-// of X-hat per CTA out of 227 KiB); the register budget follows from it.
+// CTAs that fit on one SM: by threads (2048), by shared memory (two copies of
+// X-hat per CTA out of 227 KiB) and by registers; the register budget of the
+// launch bound follows from it.
 template <class G, int M, int T>
 constexpr int mt_ctas_per_sm()
 {
     constexpr int by_threads = 2048 / T;
     constexpr int by_smem = (227 * 1024) / (2 * G::N * M * static_cast<int>(sizeof(typename G::W)) + 1024);
     constexpr int c = by_threads < by_smem ? by_threads : by_smem;
-    // with four or more CTAs one is traded for registers (no spills)
-    return c < 1 ? 1 : (c >= 4 ? c - 1 : c);
+    // at least 48 registers a thread (fewer spill)
+    constexpr int by_regs = 65536 / (T * 48);
+    constexpr int r = c < by_regs ? c : by_regs;
+    return r < 1 ? 1 : r;
 }
 
 template <class G, int M, int VW, int T, class P, bool UNITS>
@@ -485,7 +193,7 @@ __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(
                 const bool act = v * VW < hi;
                 if (act) ldv<W, VW>(cur + v * VW, w);
 #pragma unroll
-                for (int u = 0; u < VW; ++u) z[u] = act ? G::temper(w[u]) : W(0);
+                for (int u = 0; u < VW; ++u) z[u] = act ? G::temper(w[u], a.k) : W(0);
                 emit_p<P, W, VW>(plan, em, v * VW, z, p, hi, -static_cast<long long>(p), act, true);
             }
             e = hi - p;
@@ -545,7 +253,7 @@ static cudaError_t launch_mt_pu(const GenArgs& a, cudaStream_t st)
     }
     // unit launches are persistent: a few CTAs per SM pull units from the counter
     long long grid = a.gens < (1LL << 30) ? a.gens : (1LL << 30);
-    if (UNITS && a.work_counter) {
+    if (UNITS && a.work_counter && !a.cta_per_unit) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -629,7 +337,7 @@ __device__ __forceinline__ void m1_store(char* out, long long e, typename G::W z
 // the old copy, from the new one (nxt); call word e + k for k < hi
 template <class G, int DT, int K0, int K1>
 __device__ __forceinline__ void m1_phase(const typename G::W* __restrict__ cur, typename G::W* __restrict__ nxt,
-                                         char* __restrict__ out, long long e, int hi, int lane)
+                                         char* __restrict__ out, long long e, int hi, int lane, const ShiftK& sk)
 {
     constexpr int N = G::N, MM = G::MM;
     // the two copies never alias, so the loads of several words can be
@@ -638,7 +346,7 @@ __device__ __forceinline__ void m1_phase(const typename G::W* __restrict__ cur, 
     for (int k = K0 + lane; k < K1; k += 32) {
         const typename G::W x = G::twist(cur[k], k + 1 < N ? cur[k + 1] : nxt[0], k + MM < N ? cur[k + MM] : nxt[k + MM - N]);
         nxt[k] = x;
-        if (k < hi) m1_store<G, DT>(out, e + k, G::temper(x));
+        if (k < hi) m1_store<G, DT>(out, e + k, G::temper(x, sk));
     }
 }
 
@@ -691,18 +399,18 @@ __global__ void __launch_bounds__(kM1Warps * 32) gen_mt1_kernel(GenArgs a)
         if (p < N && total > 0) {
             // rest of the current block: block word k is call word k - p
             const int hi = static_cast<int>(min(static_cast<long long>(N), p + total));
-            for (int k = p + lane; k < hi; k += 32) m1_store<G, DT>(out, k - p, G::temper(cur[k]));
+            for (int k = p + lane; k < hi; k += 32) m1_store<G, DT>(out, k - p, G::temper(cur[k], a.k));
             e = hi - p;
             final_pos = hi;
         }
         while (e < total) {
             const int hi = static_cast<int>(min(static_cast<long long>(N), total - e));
-            m1_phase<G, DT, 0, NM>(cur, nxt, out, e, hi, lane);
+            m1_phase<G, DT, 0, NM>(cur, nxt, out, e, hi, lane, a.k);
             __syncwarp();
-            m1_phase<G, DT, NM, (2 * NM < N ? 2 * NM : N)>(cur, nxt, out, e, hi, lane);
+            m1_phase<G, DT, NM, (2 * NM < N ? 2 * NM : N)>(cur, nxt, out, e, hi, lane, a.k);
             __syncwarp();
             if constexpr (2 * NM < N) {
-                m1_phase<G, DT, (2 * NM < N ? 2 * NM : N), N>(cur, nxt, out, e, hi, lane);
+                m1_phase<G, DT, (2 * NM < N ? 2 * NM : N), N>(cur, nxt, out, e, hi, lane, a.k);
                 __syncwarp();
             }
             W* t = cur;
@@ -721,7 +429,7 @@ template <class G, int DT, bool UNITS>
 static cudaError_t launch_mt1_t(const GenArgs& a, cudaStream_t st)
 {
     long long grid = (a.gens + kM1Warps - 1) / kM1Warps;
-    if (UNITS && a.work_counter) {
+    if (UNITS && a.work_counter && !a.cta_per_unit) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -750,17 +458,35 @@ static bool m1_eligible(int variant, const GenArgs& a)
 }
 }  // namespace dev
 
-cudaError_t launch_generate_mt(int variant, int lanes, const GenArgs& a, cudaStream_t s)
+cudaError_t launch_generate_mtc32(int lanes, int lpc, int threads, int store, const GenArgs& a, cudaStream_t s);
+cudaError_t launch_generate_mtc64(int lanes, int lpc, int threads, int store, const GenArgs& a, cudaStream_t s);
+
+cudaError_t launch_generate_mt(int variant, int lanes, const GenArgs& a_in, cudaStream_t s)
 {
     using namespace dev;
-    // a.threads selects among the compiled CTA sizes (0: default)
-    const int t = a.threads;
+    GenArgs a = a_in;
+    a.k = kShiftK;   // the tempering's multipliers travel as kernel parameters
     if (lanes == 1 && m1_eligible(variant, a)) {
         const int d = a.seg[0].dtype;
         if (variant == VMT_MT19937_32)
             return d == VMT_U32 ? launch_mt1<MT32, VMT_U32>(a, s) : launch_mt1<MT32, VMT_F32>(a, s);
         return d == VMT_U64 ? launch_mt1<MT64, VMT_U64>(a, s)
                             : (d == VMT_F64 ? launch_mt1<MT64, VMT_F64>(a, s) : launch_mt1<MT64, VMT_F32>(a, s));
+    }
+    // a.kcfg selects among the compiled configurations of (variant, lanes)
+    const KernelCfg* cfg = kernel_cfg(variant, lanes, a.kcfg);
+    if (!cfg) cfg = kernel_cfg(variant, lanes, 0);
+    int t = 0;   // CTA size of the phase form (0: its default)
+    if (cfg && cfg->form == kChain) {
+        // unit launches (per-generator positions) keep one CTA per generator
+        if (!a.units || cfg->lpc == lanes) {
+            const cudaError_t e = variant == VMT_MT19937_32
+                                      ? launch_generate_mtc32(lanes, cfg->lpc, cfg->threads, cfg->store, a, s)
+                                      : launch_generate_mtc64(lanes, cfg->lpc, cfg->threads, cfg->store, a, s);
+            if (e != cudaErrorNotSupported) return e;
+        }
+    } else if (cfg) {
+        t = cfg->threads;
     }
     if (variant == VMT_MT19937_32) {
         switch (lanes) {

@@ -174,12 +174,13 @@ __device__ __forceinline__ void sfmt_chain_run(const uint4* pre, uint4* ring, in
     }
 }
 
-// extend the sequence: units [gen, gen + G) of the ring
+// extend the sequence: units [gen, gen + G) of the ring (the grid carries the
+// recurrence of run-time generators)
 template <class J>
-__device__ __forceinline__ void extend(typename J::U* ring, int gen, int lane);
+__device__ __forceinline__ void extend(typename J::U* ring, int gen, int lane, const JumpGrid& gr);
 
 template <>
-__device__ __forceinline__ void extend<JMT32>(uint32_t* ring, int gen, int lane)
+__device__ __forceinline__ void extend<JMT32>(uint32_t* ring, int gen, int lane, const JumpGrid&)
 {
     constexpr int RG = JMT32::RING;
     for (int u = lane; u < JMT32::G; u += 32) {
@@ -189,7 +190,7 @@ __device__ __forceinline__ void extend<JMT32>(uint32_t* ring, int gen, int lane)
 }
 
 template <>
-__device__ __forceinline__ void extend<JMT64>(unsigned long long* ring, int gen, int lane)
+__device__ __forceinline__ void extend<JMT64>(unsigned long long* ring, int gen, int lane, const JumpGrid&)
 {
     constexpr int RG = JMT64::RING;
     for (int u = lane; u < JMT64::G; u += 32) {
@@ -199,7 +200,7 @@ __device__ __forceinline__ void extend<JMT64>(unsigned long long* ring, int gen,
 }
 
 template <>
-__device__ __forceinline__ void extend<JSFMT>(uint4* ring, int gen, int lane)
+__device__ __forceinline__ void extend<JSFMT>(uint4* ring, int gen, int lane, const JumpGrid&)
 {
     // 32 elements at a time: every lane the chain-free part of one element,
     // then four lanes the chain through all 32
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(kJumpWarps * 32) jump_kernel(const JumpItem* i
     for (int i0 = 0; i0 <= deg; i0 += C) {
         const int need = i0 + C + 32 * R;
         while (gen < need) {
-            extend<J>(ring, gen, lane);
+            extend<J>(ring, gen, lane, grid);
             gen += J::G;
             __syncwarp();
         }
@@ -413,6 +414,22 @@ struct CSFMT {
     using U = uint4;
     static constexpr int N = 156, MM = 122, G = 0, R = 5, W = 16, L = 12000, PRE = 32;
 };
+// Compact forms: four warps over a ring of about 20 KB, the sequence extended
+// in several rounds.  A lane-jump takes about four times longer than in the
+// sixteen-warp form, but a CTA needs little shared memory, so it finds an SM
+// next to running generation CTAs (the server's initialisation).
+struct CMT32C {
+    using U = uint32_t;
+    static constexpr int N = 624, MM = 397, G = N - MM, R = 20, W = 4, L = 5120, PRE = 0;
+};
+struct CMT64C {
+    using U = unsigned long long;
+    static constexpr int N = 312, MM = 156, G = N - MM, R = 10, W = 4, L = 2560, PRE = 0;
+};
+struct CSFMTC {
+    using U = uint4;
+    static constexpr int N = 156, MM = 122, G = 0, R = 5, W = 4, L = 1280, PRE = 32;
+};
 // coefficients per round: the ring holds the round's window of C + 33 R units
 // plus one extension step
 template <class S> __host__ __device__ constexpr int cta_round() { return (S::L - 33 * S::R - S::G) / (S::R * S::W) * (S::R * S::W); }
@@ -426,15 +443,16 @@ __device__ __forceinline__ int wrap_sub(int p, int L) { return p >= L ? p - L : 
 // extend the ring from unit gen up to (at least) unit need; every thread
 // calls it with the same arguments and gets the same new gen
 template <class S>
-__device__ __forceinline__ int cta_extend(typename S::U* ring, int gen, int need, int tid);
+__device__ __forceinline__ int cta_extend(typename S::U* ring, int gen, int need, int tid, const JumpGrid& gr);
 
 template <class S, class T>
 __device__ __forceinline__ int cta_extend_mt(typename S::U* ring, int gen, int need, int tid)
 {
     constexpr int L = S::L;
     while (gen < need) {
-        if (tid < S::G) {
-            const int q = gen + tid;   // ring positions are taken modulo L
+        // the G new words of a step are independent; a CTA may have fewer threads
+        for (int u = tid; u < S::G; u += S::W * 32) {
+            const int q = gen + u;   // ring positions are taken modulo L
             const int k = (q - S::N) % L;
             ring[q % L] = T::twist(ring[k], ring[wrap_sub(k + 1, L)], ring[wrap_sub(k + S::MM, L)]);
         }
@@ -444,23 +462,33 @@ __device__ __forceinline__ int cta_extend_mt(typename S::U* ring, int gen, int n
     return gen;
 }
 template <>
-__device__ __forceinline__ int cta_extend<CMT32>(uint32_t* ring, int gen, int need, int tid)
+__device__ __forceinline__ int cta_extend<CMT32>(uint32_t* ring, int gen, int need, int tid, const JumpGrid&)
 {
     return cta_extend_mt<CMT32, MT32>(ring, gen, need, tid);
 }
 template <>
-__device__ __forceinline__ int cta_extend<CMT64>(unsigned long long* ring, int gen, int need, int tid)
+__device__ __forceinline__ int cta_extend<CMT64>(unsigned long long* ring, int gen, int need, int tid, const JumpGrid&)
 {
     return cta_extend_mt<CMT64, MT64>(ring, gen, need, tid);
+}
+template <>
+__device__ __forceinline__ int cta_extend<CMT32C>(uint32_t* ring, int gen, int need, int tid, const JumpGrid&)
+{
+    return cta_extend_mt<CMT32C, MT32>(ring, gen, need, tid);
+}
+template <>
+__device__ __forceinline__ int cta_extend<CMT64C>(unsigned long long* ring, int gen, int need, int tid, const JumpGrid&)
+{
+    return cta_extend_mt<CMT64C, MT64>(ring, gen, need, tid);
 }
 // SFMT: 32 elements at a time, warp 1 computing their chain-free parts into
 // the 32 units after the ring and thread 0 running the chain through them;
 // the two warps meet at named barrier 1, the other warps wait at the end
-template <>
-__device__ __forceinline__ int cta_extend<CSFMT>(uint4* ring, int gen, int need, int tid)
+template <class S>
+__device__ __forceinline__ int cta_extend_sfmt(uint4* ring, int gen, int need, int tid)
 {
-    constexpr int L = CSFMT::L, NN = CSFMT::N, MMM = CSFMT::MM;
-    static_assert(NN - MMM >= 32 && CSFMT::W >= 2, "blocks of 32 elements, two warps");
+    constexpr int L = S::L, NN = S::N, MMM = S::MM;
+    static_assert(NN - MMM >= 32 && S::W >= 2, "blocks of 32 elements, two warps");
     uint4* pre = ring + L;
     if (tid < 64) {
         uint4 c = make_uint4(0u, 0u, 0u, 0u), d = c;
@@ -485,6 +513,16 @@ __device__ __forceinline__ int cta_extend<CSFMT>(uint4* ring, int gen, int need,
     }
     __syncthreads();
     return need > gen ? need : gen;
+}
+template <>
+__device__ __forceinline__ int cta_extend<CSFMT>(uint4* ring, int gen, int need, int tid, const JumpGrid&)
+{
+    return cta_extend_sfmt<CSFMT>(ring, gen, need, tid);
+}
+template <>
+__device__ __forceinline__ int cta_extend<CSFMTC>(uint4* ring, int gen, int need, int tid, const JumpGrid&)
+{
+    return cta_extend_sfmt<CSFMTC>(ring, gen, need, tid);
 }
 
 template <class S>
@@ -514,7 +552,7 @@ __global__ void __launch_bounds__(S::W * 32) jump_cta_kernel(const JumpItem* ite
     int gen = N;
     for (int i0 = 0; i0 <= deg; i0 += C) {
         const int iend = min(i0 + C, deg + 1);
-        gen = cta_extend<S>(ring, gen, iend + 33 * R, tid);
+        gen = cta_extend<S>(ring, gen, iend + 33 * R, tid, grid);
         // this warp's slice of the round's coefficients, a multiple of R long
         const int span = ((iend - i0 + W * R - 1) / (W * R)) * R;
         const int lo = i0 + warp * span, hi = min(lo + span, iend);
@@ -546,11 +584,69 @@ __global__ void __launch_bounds__(S::W * 32) jump_cta_kernel(const JumpItem* ite
     }
 }
 
+// ---------------------------------------------------------------------------
+// twisted GFSR with run-time parameters (w <= 32, compiled n): the same
+// window-correlation kernels, with the sequence extended one word at a time
+// by the recurrence the grid carries.  Used to check the jump kernels on
+// generators small enough for the matrix route of Sec. 3.1, and for F2-linear
+// generators other than the three above.
+// ---------------------------------------------------------------------------
+template <int N_>
+struct JTG {
+    using U = uint32_t;
+    static constexpr int N = N_, MM = 1, R = 4, RING = 260, C = 128, G = 1, PRE = 0;
+};
+template <int N_>
+struct CTG {
+    using U = uint32_t;
+    static constexpr int N = N_, MM = 1, G = 1, R = 4, W = 4, L = 1024, PRE = 0;
+};
+
+__device__ __forceinline__ uint32_t tg_twist(uint32_t xk, uint32_t xk1, uint32_t xkm, const JumpGrid& g)
+{
+    const uint32_t y = (xk & g.tg_upper) | (xk1 & g.tg_lower);
+    return xkm ^ (y >> 1) ^ ((y & 1u) ? g.tg_a : 0u);
+}
+
+// one new word (lane 0) per call; the kernel's __syncwarp follows
+template <int N_>
+__device__ __forceinline__ void extend_tg(uint32_t* ring, int gen, int lane, const JumpGrid& g)
+{
+    constexpr int RG = JTG<N_>::RING;
+    if (lane == 0) {
+        const int k = gen - N_;
+        ring[gen % RG] = tg_twist(ring[k % RG], ring[(k + 1) % RG], ring[(k + static_cast<int>(g.tg_m)) % RG], g);
+    }
+}
+template <> __device__ __forceinline__ void extend<JTG<4>>(uint32_t* r, int gen, int lane, const JumpGrid& g) { extend_tg<4>(r, gen, lane, g); }
+template <> __device__ __forceinline__ void extend<JTG<5>>(uint32_t* r, int gen, int lane, const JumpGrid& g) { extend_tg<5>(r, gen, lane, g); }
+template <> __device__ __forceinline__ void extend<JTG<17>>(uint32_t* r, int gen, int lane, const JumpGrid& g) { extend_tg<17>(r, gen, lane, g); }
+
+template <int N_>
+__device__ __forceinline__ int cta_extend_tg(uint32_t* ring, int gen, int need, int tid, const JumpGrid& g)
+{
+    constexpr int L = CTG<N_>::L;
+    for (; gen < need; ++gen) {
+        if (tid == 0) {
+            const int k = gen - N_;
+            ring[gen % L] = tg_twist(ring[k % L], ring[(k + 1) % L], ring[(k + static_cast<int>(g.tg_m)) % L], g);
+        }
+        __syncthreads();
+    }
+    return gen;
+}
+template <> __device__ __forceinline__ int cta_extend<CTG<4>>(uint32_t* r, int gen, int need, int tid, const JumpGrid& g) { return cta_extend_tg<4>(r, gen, need, tid, g); }
+template <> __device__ __forceinline__ int cta_extend<CTG<5>>(uint32_t* r, int gen, int need, int tid, const JumpGrid& g) { return cta_extend_tg<5>(r, gen, need, tid, g); }
+template <> __device__ __forceinline__ int cta_extend<CTG<17>>(uint32_t* r, int gen, int need, int tid, const JumpGrid& g) { return cta_extend_tg<17>(r, gen, need, tid, g); }
+
 // Launches of fewer items than this use the CTA-per-item kernel, per variant
 // (the crossover in lane-jumps per second measured on GB300: about 4096 for
 // MT19937-32/64, about 512 for SFMT19937, whose serial chain makes the CTA
 // kernel's lane-jump long).
 static std::atomic<long long> g_split_below[3] = {{4096}, {4096}, {512}};
+// every launch of the variant in the compact CTA form (callers that share the
+// GPU with long-running kernels; tests)
+static std::atomic<bool> g_compact[3] = {{false}, {false}, {false}};
 
 // the CTA kernels' dynamic shared memory limit, raised once per device
 template <class S>
@@ -568,11 +664,17 @@ static cudaError_t cta_smem_attr()
     return e;
 }
 
-template <class J, class S>
-static cudaError_t launch_jump_t(const JumpItem* items, const JumpGrid& gr, long long nitems, const uint32_t* polys,
-                                 cudaStream_t st, long long split_below)
+template <class J, class S, class SC>
+static cudaError_t launch_jump_t(int variant, const JumpItem* items, const JumpGrid& gr, long long nitems,
+                                 const uint32_t* polys, cudaStream_t st, long long split_below, bool compact)
 {
     if (nitems <= 0) return cudaSuccess;
+    if (compact || g_compact[variant].load(std::memory_order_relaxed)) {
+        const cudaError_t e = cta_smem_attr<SC>();
+        if (e != cudaSuccess) return e;
+        jump_cta_kernel<SC><<<static_cast<unsigned>(nitems), SC::W * 32, cta_smem<SC>(), st>>>(items, gr, polys);
+        return cudaGetLastError();
+    }
     if (nitems < split_below) {
         const cudaError_t e = cta_smem_attr<S>();
         if (e != cudaSuccess) return e;
@@ -635,28 +737,62 @@ cudaError_t launch_seed(int variant, long long count, const unsigned long long* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s)
+cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s,
+                        bool compact)
 {
     using namespace dev;
     if (variant < 0 || variant > 2) return cudaErrorInvalidValue;
     const JumpGrid none{};
     const long long sb = g_split_below[variant].load(std::memory_order_relaxed);
-    if (variant == VMT_MT19937_32) return launch_jump_t<JMT32, CMT32>(items, none, nitems, polys, s, sb);
-    if (variant == VMT_MT19937_64) return launch_jump_t<JMT64, CMT64>(items, none, nitems, polys, s, sb);
-    return launch_jump_t<JSFMT, CSFMT>(items, none, nitems, polys, s, sb);
+    if (variant == VMT_MT19937_32) return launch_jump_t<JMT32, CMT32, CMT32C>(variant, items, none, nitems, polys, s, sb, compact);
+    if (variant == VMT_MT19937_64) return launch_jump_t<JMT64, CMT64, CMT64C>(variant, items, none, nitems, polys, s, sb, compact);
+    return launch_jump_t<JSFMT, CSFMT, CSFMTC>(variant, items, none, nitems, polys, s, sb, compact);
 }
 
-cudaError_t launch_jump_grid(int variant, const JumpGrid& gr, long long nitems, const uint32_t* polys, cudaStream_t s)
+cudaError_t launch_jump_grid(int variant, const JumpGrid& gr, long long nitems, const uint32_t* polys, cudaStream_t s,
+                             bool compact)
 {
     using namespace dev;
     if (variant < 0 || variant > 2) return cudaErrorInvalidValue;
     const long long sb = g_split_below[variant].load(std::memory_order_relaxed);
-    if (variant == VMT_MT19937_32) return launch_jump_t<JMT32, CMT32>(nullptr, gr, nitems, polys, s, sb);
-    if (variant == VMT_MT19937_64) return launch_jump_t<JMT64, CMT64>(nullptr, gr, nitems, polys, s, sb);
-    return launch_jump_t<JSFMT, CSFMT>(nullptr, gr, nitems, polys, s, sb);
+    if (variant == VMT_MT19937_32) return launch_jump_t<JMT32, CMT32, CMT32C>(variant, nullptr, gr, nitems, polys, s, sb, compact);
+    if (variant == VMT_MT19937_64) return launch_jump_t<JMT64, CMT64, CMT64C>(variant, nullptr, gr, nitems, polys, s, sb, compact);
+    return launch_jump_t<JSFMT, CSFMT, CSFMTC>(variant, nullptr, gr, nitems, polys, s, sb, compact);
+}
+
+namespace dev {
+template <int N>
+static cudaError_t launch_tg_n(bool cta, const JumpItem* items, long long nitems, const JumpGrid& gr,
+                               const uint32_t* polys, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    if (cta) {
+        const cudaError_t e = cta_smem_attr<CTG<N>>();
+        if (e != cudaSuccess) return e;
+        jump_cta_kernel<CTG<N>><<<static_cast<unsigned>(nitems), CTG<N>::W * 32, cta_smem<CTG<N>>(), st>>>(items, gr,
+                                                                                                          polys);
+    } else {
+        const long long grid = (nitems + kJumpWarps - 1) / kJumpWarps;
+        jump_kernel<JTG<N>><<<static_cast<unsigned>(grid), kJumpWarps * 32, 0, st>>>(items, gr, nitems, polys);
+    }
+    return cudaGetLastError();
+}
+}  // namespace dev
+
+cudaError_t launch_tgfsr_jump(int n, bool cta, const JumpItem* items, long long nitems, const JumpGrid& gr,
+                              const uint32_t* polys, cudaStream_t s)
+{
+    switch (n) {
+    case 4: return dev::launch_tg_n<4>(cta, items, nitems, gr, polys, s);
+    case 5: return dev::launch_tg_n<5>(cta, items, nitems, gr, polys, s);
+    case 17: return dev::launch_tg_n<17>(cta, items, nitems, gr, polys, s);
+    }
+    return cudaErrorNotSupported;
 }
 
 void set_jump_split_below(int variant, long long items) { dev::g_split_below[variant].store(items < 0 ? 0 : items); }
+void set_jump_compact(int variant, bool on) { dev::g_compact[variant].store(on); }
+bool get_jump_compact(int variant) { return dev::g_compact[variant].load(); }
 long long get_jump_split_below(int variant) { return dev::g_split_below[variant].load(); }
 
 cudaError_t launch_fill_int(int* p, long long n, int value, cudaStream_t s)

@@ -199,7 +199,7 @@ int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
         const int nsub = static_cast<int>(counts.size());
         std::vector<vmt_state*> sts(static_cast<size_t>(nsub), nullptr);
         rc = vmt::init_multi_impl(sts.data(), variant, nsub, lanes_of.data(), counts.data(), sl.h_seeds + seed0,
-                                  sl.h_jumps + seed0, s_init, true, s->pool);
+                                  sl.h_jumps + seed0, s_init, true, s->pool, true);
         if (rc) return rc;
         for (vmt_state* st : sts) b->states.push_back(st);
         seed0 += k_all;
@@ -239,7 +239,7 @@ int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
                 cudaMemcpyAsync(sl.d_map + map0, sl.h_map + map0, static_cast<size_t>(nchunk) * sizeof(int2),
                                 cudaMemcpyHostToDevice, s_init);
                 rc = vmt::launch_chunk_jumps(sts[static_cast<size_t>(gi)], csts[static_cast<size_t>(gi)],
-                                             sl.d_map + map0, s_init);
+                                             sl.d_map + map0, s_init, true);
                 if (rc) return rc;
             }
             map0 += nchunk;
@@ -290,7 +290,8 @@ int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
                 std::memcpy(sl.h_units + unit0, units.data(), static_cast<size_t>(nu) * sizeof(vmt::UnitDesc));
                 cudaMemcpyAsync(sl.d_units + unit0, sl.h_units + unit0,
                                 static_cast<size_t>(nu) * sizeof(vmt::UnitDesc), cudaMemcpyHostToDevice, s_gen);
-                rc = vmt::launch_unit_table(variant, lanes, dtype, sl.d_units + unit0, nu, sl.d_counter + gk, s_gen);
+                rc = vmt::launch_unit_table(variant, lanes, dtype, sl.d_units + unit0, nu, sl.d_counter + gk, s_gen,
+                                            true);
                 if (rc) return rc;
             }
             unit0 += nu;
@@ -498,14 +499,19 @@ int vmt_server_create(vmt_server** out, const vmt_server_config* cfg)
         ok = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess &&
              cudaStreamCreateWithFlags(&s->s_free, cudaStreamNonBlocking) == cudaSuccess;
     }
+    // three priorities: the express slot's work above the regular slots'
+    // initialisation (short jump launches), above the regular generation
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    const int prio_init = prio_hi < prio_lo ? prio_hi + 1 : prio_hi;   // greater priority = smaller number
     for (int i = 0; i < kSlots && ok; ++i) {
         Slot& sl = s->slots[i];
         const size_t n = static_cast<size_t>(cfg->max_batch);
         const size_t nu = static_cast<size_t>(kMaxUnits);
         // initialisation (short jump launches) is scheduled ahead of generation
-        // blocks still waiting for an SM; so is the express slot's generation
+        // blocks still waiting for an SM (every generation unit has its own
+        // CTA, so an SM frees up whenever one finishes); the express slot's
+        // initialisation and generation go ahead of both
         ok = cudaStreamCreateWithPriority(&sl.s_gen, cudaStreamNonBlocking, i == kExpress ? prio_hi : prio_lo) ==
                  cudaSuccess &&
              cudaHostAlloc(reinterpret_cast<void**>(&sl.h_units), nu * sizeof(vmt::UnitDesc), 0) == cudaSuccess &&
@@ -518,7 +524,8 @@ int vmt_server_create(vmt_server** out, const vmt_server_config* cfg)
         for (int e = 0; e < 3 && ok; ++e)
             ok = cudaEventCreate(&sl.ev[e]) == cudaSuccess &&
                  cudaEventCreateWithFlags(&sl.ev_init[e], cudaEventDisableTiming) == cudaSuccess &&
-                 cudaStreamCreateWithPriority(&sl.s_init[e], cudaStreamNonBlocking, prio_hi) == cudaSuccess;
+                 cudaStreamCreateWithPriority(&sl.s_init[e], cudaStreamNonBlocking,
+                                              i == kExpress ? prio_hi : prio_init) == cudaSuccess;
     }
     if (ok && cfg->reserve) {
         // map the budgets now: one allocation of their sum, freed back to the pool

@@ -44,27 +44,30 @@ thread_local std::string g_err;
 void vmt::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
 // ---------------------------------------------------------------------------
-// tuning table: CTA size of the generation kernels per (variant, lanes)
+// tuning table: compiled kernel configuration per (variant, lanes), an index
+// into that pair's rows of vmt::kKernelCfgs (0: the default)
 // ---------------------------------------------------------------------------
 namespace {
 std::mutex g_tune_lock;
-int g_tune_threads[3][17] = {};
+int g_tune_kcfg[3][17] = {};
 bool g_tune_env_read = false;
 
-// the CTA sizes compiled for each (variant, lanes); the first is the default
-std::vector<int> tune_candidates(int variant, int lanes)
+// candidate index of the phase-form kernel with `threads` threads (-1: none)
+int phase_index(int variant, int lanes, int threads)
 {
-    if (variant == VMT_SFMT19937) return {};
-    if (lanes == 8) return {256, 512};
-    if (lanes == 16) return {512, 1024};
-    return {};
+    const int n = vmt::kernel_cfg_count(variant, lanes);
+    for (int i = 0; i < n; ++i) {
+        const vmt::KernelCfg* c = vmt::kernel_cfg(variant, lanes, i);
+        if (c->form == vmt::kPhase && c->threads == threads) return i;
+    }
+    return -1;
 }
 
 void read_tune_env_locked()
 {
     if (g_tune_env_read) return;
     g_tune_env_read = true;
-    // VMT_TUNE="mt32:16:1024,mt64:8:512"
+    // VMT_TUNE="mt32:16:1024,mt64:8:#2": a phase-form CTA size, or #index
     const char* e = std::getenv("VMT_TUNE");
     if (!e) return;
     std::string s(e);
@@ -73,14 +76,18 @@ void read_tune_env_locked()
         size_t j = s.find(',', i);
         if (j == std::string::npos) j = s.size();
         const std::string item = s.substr(i, j - i);
-        int lanes = 0, threads = 0;
+        int lanes = 0, val = 0;
         char name[8] = {0};
-        if (std::sscanf(item.c_str(), "%7[a-z0-9]:%d:%d", name, &lanes, &threads) == 3 && lanes >= 0 && lanes <= 16) {
+        bool by_index = false;
+        bool ok = std::sscanf(item.c_str(), "%7[a-z0-9]:%d:#%d", name, &lanes, &val) == 3;
+        if (ok) by_index = true;
+        else ok = std::sscanf(item.c_str(), "%7[a-z0-9]:%d:%d", name, &lanes, &val) == 3;
+        if (ok && lanes >= 0 && lanes <= 16) {
             const std::string n(name);
             const int v = n == "mt32" ? 0 : (n == "mt64" ? 1 : (n == "sfmt" ? 2 : -1));
             if (v >= 0) {
-                const auto c = tune_candidates(v, lanes);
-                if (std::find(c.begin(), c.end(), threads) != c.end()) g_tune_threads[v][lanes] = threads;
+                const int idx = by_index ? val : phase_index(v, lanes, val);
+                if (idx >= 0 && idx < vmt::kernel_cfg_count(v, lanes)) g_tune_kcfg[v][lanes] = idx;
             }
         }
         i = j + 1;
@@ -88,12 +95,12 @@ void read_tune_env_locked()
 }
 }  // namespace
 
-int vmt::tuned_threads(int variant, int lanes)
+int vmt::tuned_kcfg(int variant, int lanes)
 {
     if (variant < 0 || variant > 2 || lanes < 0 || lanes > 16) return 0;
     std::lock_guard<std::mutex> lk(g_tune_lock);
     read_tune_env_locked();
-    return g_tune_threads[variant][lanes];
+    return g_tune_kcfg[variant][lanes];
 }
 
 namespace {
@@ -438,9 +445,10 @@ namespace {
 
 int64_t state_total_bytes(const vmt_state* st) { return st->count * vmt::state_bytes_per_gen(st->variant, st->lanes); }
 
-int run_jump_grid(int variant, const vmt::JumpGrid& gr, long long nitems, const uint32_t* table, cudaStream_t s)
+int run_jump_grid(int variant, const vmt::JumpGrid& gr, long long nitems, const uint32_t* table, cudaStream_t s,
+                  bool compact = false)
 {
-    CUDA_TRY(vmt::launch_jump_grid(variant, gr, nitems, table, s));
+    CUDA_TRY(vmt::launch_jump_grid(variant, gr, nitems, table, s, compact));
     return VMT_OK;
 }
 
@@ -523,19 +531,20 @@ int reserve_units(vmt::UnitDesc** h, vmt::UnitDesc** d, int** counter, int64_t* 
 }  // namespace
 
 int vmt::launch_unit_table(int variant, int lanes, int dtype, const vmt::UnitDesc* d_units, int64_t n, int* counter,
-                           void* stream)
+                           void* stream, bool cta_per_unit)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n == 0) return VMT_OK;
     vmt::GenArgs a{};
     a.gens = n;
-    a.threads = vmt::tuned_threads(variant, lanes);
+    a.kcfg = vmt::tuned_kcfg(variant, lanes);
     a.nseg = 1;
     a.seg[0].dtype = dtype;
     a.seg[0].wbeg = 0;
     a.seg[0].wend = kMaxUnitWords;
     a.units = d_units;
     a.work_counter = counter;
+    a.cta_per_unit = cta_per_unit ? 1 : 0;
     CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
     CUDA_TRY(vmt::launch_generate(variant, lanes, a, true, s));
     return VMT_OK;
@@ -563,7 +572,7 @@ int generate_range(vmt_state* st, int64_t g0, int64_t gens, int nseg, const int6
     a.states = static_cast<char*>(st->d_states) + g0 * vmt::state_bytes_per_gen(v, st->lanes);
     a.gens = gens;
     a.gen0 = 0;
-    a.threads = vmt::tuned_threads(v, st->lanes);
+    a.kcfg = vmt::tuned_kcfg(v, st->lanes);
     a.pos_dev = st->d_pos + g0;
     a.pos = static_cast<int>(st->h_pos[static_cast<size_t>(g0)]);
     a.nseg = nseg;
@@ -723,7 +732,7 @@ int vmt_set_cache_dir(const char* path)
 // null); free such objects with vmt::free_state_async.
 int vmt::init_multi_impl(vmt_state** outs, int variant, int nsub, const int* lanes, const int64_t* counts,
                          const uint64_t* seeds, const uint64_t* jumps, void* cuda_stream, bool async_alloc,
-                         cudaMemPool_t pool)
+                         cudaMemPool_t pool, bool compact_jumps)
 {
     if (!outs || !lanes || !counts || nsub < 1) return fail(VMT_EINVAL, "null argument");
     for (int i = 0; i < nsub; ++i) outs[i] = nullptr;
@@ -804,7 +813,7 @@ int vmt::init_multi_impl(vmt_state** outs, int variant, int nsub, const int* lan
             for (int64_t g = 0; g < total && !used; ++g) used = ((jumps[g] >> (8 * i)) & 255u) != 0;
             if (!used) continue;
             gr.digit = i;
-            if ((rc = run_jump_grid(variant, gr, total, c.d_table, s))) return rc;
+            if ((rc = run_jump_grid(variant, gr, total, c.d_table, s, compact_jumps))) return rc;
         }
     }
     // lane fan-out per object: lane t = x^(t J)(F) base, written into X-hat's
@@ -816,7 +825,7 @@ int vmt::init_multi_impl(vmt_state** outs, int variant, int nsub, const int* lan
         gr.lanes = lanes[i];
         gr.states = static_cast<char*>(made[static_cast<size_t>(i)]->d_states);
         gr.gen_bytes = vmt::state_bytes_per_gen(variant, lanes[i]);
-        if ((rc = run_jump_grid(variant, gr, counts[i] * lanes[i], c.d_table, s))) return rc;
+        if ((rc = run_jump_grid(variant, gr, counts[i] * lanes[i], c.d_table, s, compact_jumps))) return rc;
         g0 += counts[i];
     }
     CUDA_TRY(cudaFreeAsync(d_seeds, s));
@@ -863,7 +872,8 @@ int vmt::alloc_states_async(vmt_state** out, int variant, int lanes, int64_t cou
     return VMT_OK;
 }
 
-int vmt::launch_chunk_jumps(const vmt_state* requests, vmt_state* chunks, const int2* d_map, void* cuda_stream)
+int vmt::launch_chunk_jumps(const vmt_state* requests, vmt_state* chunks, const int2* d_map, void* cuda_stream,
+                            bool compact_jumps)
 {
     const int variant = requests->variant;
     int rc = ensure_chunks(variant);
@@ -880,7 +890,8 @@ int vmt::launch_chunk_jumps(const vmt_state* requests, vmt_state* chunks, const 
     gr.row_deg = c.d_row_deg;
     gr.chunk_map = d_map;
     gr.chunk_row0 = kChunkRow0;
-    return run_jump_grid(variant, gr, chunks->count * requests->lanes, c.d_table, static_cast<cudaStream_t>(cuda_stream));
+    return run_jump_grid(variant, gr, chunks->count * requests->lanes, c.d_table, static_cast<cudaStream_t>(cuda_stream),
+                         compact_jumps);
 }
 
 void vmt::free_state_async(vmt_state* st, void* cuda_stream)
@@ -1094,6 +1105,16 @@ int64_t vmt_tune_jump_get(int variant)
 {
     if (!valid_variant(variant)) return fail(VMT_EINVAL, "bad variant");
     return vmt::get_jump_split_below(variant);
+}
+
+int vmt_tune_jump_compact(int variant, int on)
+{
+    if (variant < -1 || variant > 2) return fail(VMT_EINVAL, "bad variant");
+    const int old = variant < 0 ? vmt::get_jump_compact(0) : vmt::get_jump_compact(variant);
+    if (on >= 0)
+        for (int v = 0; v < 3; ++v)
+            if (variant < 0 || v == variant) vmt::set_jump_compact(v, on != 0);
+    return old ? 1 : 0;
 }
 
 int vmt_prepare(int variant, void* cuda_stream)
@@ -1589,19 +1610,51 @@ void vmt_free(vmt_state* st)
 int vmt_tune_set(int variant, int lanes, int threads)
 {
     if (!valid_variant(variant) || !valid_lanes(lanes)) return fail(VMT_EINVAL, "bad variant or lanes");
-    const auto c = tune_candidates(variant, lanes);
-    if (threads != 0 && std::find(c.begin(), c.end(), threads) == c.end())
-        return fail(VMT_EINVAL, "no kernel compiled with that CTA size for this variant and lane count");
+    const int idx = threads == 0 ? 0 : phase_index(variant, lanes, threads);
+    if (idx < 0) return fail(VMT_EINVAL, "no kernel compiled with that CTA size for this variant and lane count");
     std::lock_guard<std::mutex> lk(g_tune_lock);
     read_tune_env_locked();
-    g_tune_threads[variant][lanes] = threads;
+    g_tune_kcfg[variant][lanes] = idx;
     return VMT_OK;
 }
 
 int vmt_tune_get(int variant, int lanes)
 {
     if (!valid_variant(variant) || !valid_lanes(lanes)) return fail(VMT_EINVAL, "bad variant or lanes");
-    return vmt::tuned_threads(variant, lanes);
+    const vmt::KernelCfg* c = vmt::kernel_cfg(variant, lanes, vmt::tuned_kcfg(variant, lanes));
+    return c ? c->threads : 0;
+}
+
+int vmt_tune_kernels(int variant, int lanes, int* desc, int cap)
+{
+    if (!valid_variant(variant) || !valid_lanes(lanes) || cap < 0 || (cap > 0 && !desc))
+        return fail(VMT_EINVAL, "bad variant, lanes or buffer");
+    const int n = vmt::kernel_cfg_count(variant, lanes);
+    for (int i = 0; i < n && i < cap; ++i) {
+        const vmt::KernelCfg* c = vmt::kernel_cfg(variant, lanes, i);
+        desc[4 * i + 0] = c->form;
+        desc[4 * i + 1] = c->lpc;
+        desc[4 * i + 2] = c->threads;
+        desc[4 * i + 3] = c->store;
+    }
+    return n;
+}
+
+int vmt_tune_set_kernel(int variant, int lanes, int index)
+{
+    if (!valid_variant(variant) || !valid_lanes(lanes)) return fail(VMT_EINVAL, "bad variant or lanes");
+    const int n = vmt::kernel_cfg_count(variant, lanes);
+    if (index < 0 || (index > 0 && index >= n)) return fail(VMT_EINVAL, "no compiled kernel configuration with that index");
+    std::lock_guard<std::mutex> lk(g_tune_lock);
+    read_tune_env_locked();
+    g_tune_kcfg[variant][lanes] = index;
+    return VMT_OK;
+}
+
+int vmt_tune_get_kernel(int variant, int lanes)
+{
+    if (!valid_variant(variant) || !valid_lanes(lanes)) return fail(VMT_EINVAL, "bad variant or lanes");
+    return vmt::tuned_kcfg(variant, lanes);
 }
 
 int vmt_tune_save(const char* path)
@@ -1612,10 +1665,13 @@ int vmt_tune_save(const char* path)
     {
         std::lock_guard<std::mutex> lk(g_tune_lock);
         read_tune_env_locked();
-        std::fprintf(f, "# variant lanes threads\n");
+        std::fprintf(f, "# variant lanes form lanes_per_cta threads store_bytes\n");
         for (int v = 0; v < 3; ++v)
             for (int m = 1; m <= 16; m *= 2)
-                if (g_tune_threads[v][m]) std::fprintf(f, "%d %d %d\n", v, m, g_tune_threads[v][m]);
+                if (g_tune_kcfg[v][m]) {
+                    const vmt::KernelCfg* c = vmt::kernel_cfg(v, m, g_tune_kcfg[v][m]);
+                    if (c) std::fprintf(f, "%d %d %d %d %d %d\n", v, m, c->form, c->lpc, c->threads, c->store);
+                }
     }
     const bool ok = std::fclose(f) == 0;
     return ok ? VMT_OK : fail(VMT_EINVAL, std::string("cannot write ") + path);
@@ -1626,27 +1682,39 @@ int vmt_tune_load(const char* path)
     if (!path) return fail(VMT_EINVAL, "null path");
     FILE* f = std::fopen(path, "r");
     if (!f) return fail(VMT_EINVAL, std::string("cannot read ") + path);
-    char line[128];
+    char line[160];
     int bad = 0;
     while (std::fgets(line, sizeof(line), f)) {
         if (line[0] == '#' || line[0] == '\n') continue;
-        int v = -1, m = 0, t = -1;
-        if (std::sscanf(line, "%d %d %d", &v, &m, &t) != 3 || vmt_tune_set(v, m, t) != VMT_OK) ++bad;
+        int v = -1, m = 0, form = -1, lpc = 0, t = -1, store = 0;
+        const int k = std::sscanf(line, "%d %d %d %d %d %d", &v, &m, &form, &lpc, &t, &store);
+        if (k == 3) {   // "variant lanes threads": a phase-form CTA size
+            if (vmt_tune_set(v, m, form) != VMT_OK) ++bad;
+        } else if (k == 6 && valid_variant(v) && valid_lanes(m)) {
+            int idx = -1;
+            for (int i = 0; i < vmt::kernel_cfg_count(v, m); ++i) {
+                const vmt::KernelCfg* c = vmt::kernel_cfg(v, m, i);
+                if (c->form == form && c->lpc == lpc && c->threads == t && c->store == store) idx = i;
+            }
+            if (idx < 0 || vmt_tune_set_kernel(v, m, idx) != VMT_OK) ++bad;
+        } else {
+            ++bad;
+        }
     }
     std::fclose(f);
     return bad ? fail(VMT_EINVAL, "tuning file has entries that match no compiled kernel") : VMT_OK;
 }
 
-int vmt_autotune_multi(int variant, int lanes, int64_t count, int nseg, const int64_t* counts, const int* dtypes,
-                       int reps, void* cuda_stream, int* best_threads, double* best_ms)
+int vmt_autotune_grid(int variant, int lanes, int64_t count, int nseg, const int64_t* counts, const int* dtypes,
+                      int reps, void* cuda_stream, double* ms_out, int cap, int* best_index)
 {
     if (!valid_variant(variant) || !valid_lanes(lanes) || count < 1 || reps < 1 || nseg < 1 || nseg > VMT_MAXSEG ||
-        !counts || !dtypes)
+        !counts || !dtypes || cap < 0 || (cap > 0 && !ms_out))
         return fail(VMT_EINVAL, "bad autotune arguments");
     for (int i = 0; i < nseg; ++i)
         if (counts[i] < 1 || dtypes[i] < VMT_U32 || dtypes[i] > VMT_F64) return fail(VMT_EINVAL, "bad autotune segment");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const auto cands = tune_candidates(variant, lanes);
+    const int ncand = std::max(1, vmt::kernel_cfg_count(variant, lanes));
     std::vector<uint64_t> seeds(static_cast<size_t>(count));
     for (int64_t g = 0; g < count; ++g) seeds[static_cast<size_t>(g)] = 0x9E3779B97F4A7C15ull * static_cast<uint64_t>(g + 1);
     vmt_state* st = nullptr;
@@ -1665,15 +1733,15 @@ int vmt_autotune_multi(int variant, int lanes, int64_t count, int nseg, const in
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const std::vector<int> tried = cands.empty() ? std::vector<int>{0} : cands;
+    const int prev = vmt::tuned_kcfg(variant, lanes);
     // two alternating rounds over the candidates, each candidate's time the
     // mean of `reps` calls after a warm-up; a candidate keeps its better round
-    std::vector<double> t_best(tried.size(), 1e30);
+    std::vector<double> t_best(static_cast<size_t>(ncand), 1e30);
     for (int round = 0; round < 2 && rc == VMT_OK; ++round)
-        for (size_t k = 0; k < tried.size() && rc == VMT_OK; ++k) {
+        for (int k = 0; k < ncand && rc == VMT_OK; ++k) {
             {
                 std::lock_guard<std::mutex> lk(g_tune_lock);
-                g_tune_threads[variant][lanes] = tried[k];
+                g_tune_kcfg[variant][lanes] = k;
             }
             rc = vmt_generate_multi(st, nseg, counts, dtypes, outs.data(), cuda_stream);   // warm-up
             if (rc) break;
@@ -1684,26 +1752,35 @@ int vmt_autotune_multi(int variant, int lanes, int64_t count, int nseg, const in
             cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            t_best[k] = std::min(t_best[k], static_cast<double>(ms) / reps);
+            t_best[static_cast<size_t>(k)] = std::min(t_best[static_cast<size_t>(k)], static_cast<double>(ms) / reps);
         }
     int best = 0;
-    double best_t = 1e30;
-    for (size_t k = 0; k < tried.size(); ++k)
-        if (t_best[k] < best_t) {
-            best_t = t_best[k];
-            best = tried[k];
-        }
+    for (int k = 1; k < ncand; ++k)
+        if (t_best[static_cast<size_t>(k)] < t_best[static_cast<size_t>(best)]) best = k;
     {
         std::lock_guard<std::mutex> lk(g_tune_lock);
-        g_tune_threads[variant][lanes] = best;
+        g_tune_kcfg[variant][lanes] = rc == VMT_OK ? best : prev;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (void* o : outs) cudaFree(o);
     vmt_free(st);
     if (rc) return rc;
-    if (best_threads) *best_threads = best;
-    if (best_ms) *best_ms = best_t;
+    for (int k = 0; k < ncand && k < cap; ++k) ms_out[k] = t_best[static_cast<size_t>(k)];
+    if (best_index) *best_index = best;
+    return VMT_OK;
+}
+
+int vmt_autotune_multi(int variant, int lanes, int64_t count, int nseg, const int64_t* counts, const int* dtypes,
+                       int reps, void* cuda_stream, int* best_threads, double* best_ms)
+{
+    double ms[64];
+    int best = 0;
+    const int rc = vmt_autotune_grid(variant, lanes, count, nseg, counts, dtypes, reps, cuda_stream, ms, 64, &best);
+    if (rc) return rc;
+    const vmt::KernelCfg* c = vmt::kernel_cfg(variant, lanes, best);
+    if (best_threads) *best_threads = c ? c->threads : 0;
+    if (best_ms) *best_ms = ms[best];
     return VMT_OK;
 }
 

@@ -30,59 +30,92 @@ namespace dev {
 // ----------------------------------------------------------------------------
 // generator constants
 // ----------------------------------------------------------------------------
-// Exact right shift by s (0 < s < 32) as the high word of y * 2^(32-s): it
-// runs on the multiply-add pipe instead of the shift/logic pipe, which the XORs
-// of the tempering already keep busy.
-template <int S>
-__device__ __forceinline__ uint32_t shr_mulhi(uint32_t y)
-{
-    uint32_t r;
-    asm("mul.hi.u32 %0, %1, %2;" : "=r"(r) : "r"(y), "r"(1u << (32 - S)));
-    return r;
-}
-
-// all ones when the lowest bit of x is set, else zero (x << 31, then the high
-// word of the signed product by 2), also on the multiply-add pipe
-__device__ __forceinline__ uint32_t low_bit_mask(uint32_t x)
-{
-    uint32_t t, r;
-    asm("mul.lo.u32 %0, %1, %2;" : "=r"(t) : "r"(x), "r"(0x80000000u));
-    asm("mul.hi.s32 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(2));
-    return r;
-}
+// Pipe balance.  The twist and the tempering are logic operations and
+// constant shifts, which share the ALU pipe; on MT19937-64 generation that
+// pipe is the bound, while the multiply-add pipe has room.  A left shift by s
+// is a multiplication by 2^s, but the compiler turns a multiplication by a
+// known power of two back into a shift, so the tempering takes its
+// multipliers from ShiftK, which every launch passes as a kernel parameter
+// (an operand the compiler cannot see through).  The multiplication by the
+// twist constant a (y odd ? a : 0 = (y & 1) * a) is not a power of two and
+// stays on the multiply-add pipe by itself.  Right shifts stay on the ALU
+// pipe: a multiply-high runs at half the multiply-add rate.
 
 struct MT32 {
     using W = uint32_t;
     static constexpr int N = 624, MM = 397;
+    // eq. (step) with y * A of eq. (matmult): y >> 1, XOR a when y is odd;
+    // y's lowest bit is the lowest bit of x_{k+1}
     static __device__ __forceinline__ W twist(W xk, W xk1, W xkm)
     {
         const W y = (xk & 0x80000000u) | (xk1 & 0x7FFFFFFFu);
-        // y * A: y >> 1, XOR a when y is odd; y's lowest bit is xk1's lowest bit
-        return xkm ^ shr_mulhi<1>(y) ^ (low_bit_mask(xk1) & 0x9908B0DFu);
+        return xkm ^ (y >> 1) ^ ((xk1 & 1u) * 0x9908B0DFu);
     }
+    // eq. (tempering) with (u, s, b, t, c, l) = (11, 7, 9D2C5680, 15, EFC60000, 18)
     static __device__ __forceinline__ W temper(W y)
     {
-        y ^= shr_mulhi<11>(y);
+        y ^= y >> 11;
         y ^= (y << 7) & 0x9D2C5680u;
         y ^= (y << 15) & 0xEFC60000u;
-        return y ^ shr_mulhi<18>(y);
+        return y ^ (y >> 18);
     }
+    static __device__ __forceinline__ W temper(W y, const ShiftK& k)
+    {
+        y ^= y >> 11;
+        y ^= (y * k.p7) & 0x9D2C5680u;
+        y ^= (y * k.p15) & 0xEFC60000u;
+        return y ^ (y >> 18);
+    }
+    static __device__ __forceinline__ W twist(W xk, W xk1, W xkm, const ShiftK&) { return twist(xk, xk1, xkm); }
 };
+
+// MT19937-64 on 32-bit halves (lo, hi): every 64-bit shift by a constant is
+// one funnel shift plus one 32-bit shift, every mask one operation per half.
+__device__ __forceinline__ uint32_t lo32(unsigned long long x) { return static_cast<uint32_t>(x); }
+__device__ __forceinline__ uint32_t hi32(unsigned long long x) { return static_cast<uint32_t>(x >> 32); }
+__device__ __forceinline__ unsigned long long pack64(uint32_t lo, uint32_t hi)
+{
+    return (static_cast<unsigned long long>(hi) << 32) | lo;
+}
 
 struct MT64 {
     using W = unsigned long long;
     static constexpr int N = 312, MM = 156;
+    // eq. (step), w = 64: y = upper 33 bits of x_k | lower 31 of x_{k+1}
     static __device__ __forceinline__ W twist(W xk, W xk1, W xkm)
     {
-        const W y = (xk & 0xFFFFFFFF80000000ull) | (xk1 & 0x7FFFFFFFull);
-        return xkm ^ (y >> 1) ^ ((xk1 & 1ull) * 0xB5026F5AA96619E9ull);
+        const uint32_t ylo = (lo32(xk) & 0x80000000u) | (lo32(xk1) & 0x7FFFFFFFu);
+        const uint32_t yhi = hi32(xk);
+        const uint32_t bit = lo32(xk1) & 1u;
+        const uint32_t lo = lo32(xkm) ^ __funnelshift_r(ylo, yhi, 1) ^ (bit * 0xA96619E9u);
+        const uint32_t hi = hi32(xkm) ^ (yhi >> 1) ^ (bit * 0xB5026F5Au);
+        return pack64(lo, hi);
     }
+    static __device__ __forceinline__ W twist(W xk, W xk1, W xkm, const ShiftK&) { return twist(xk, xk1, xkm); }
+    // eq. (tempering), w = 64: (u, d, s, b, t, c, l) = (29, 5555555555555555,
+    // 17, 71D67FFFEDA60000, 37, FFF7EEE000000000, 43)
     static __device__ __forceinline__ W temper(W y)
     {
         y ^= (y >> 29) & 0x5555555555555555ull;
         y ^= (y << 17) & 0x71D67FFFEDA60000ull;
         y ^= (y << 37) & 0xFFF7EEE000000000ull;
         return y ^ (y >> 43);
+    }
+    static __device__ __forceinline__ W temper(W y, const ShiftK& k)
+    {
+        uint32_t lo = lo32(y), hi = hi32(y);
+        // y ^= (y >> 29) & d
+        lo ^= __funnelshift_r(lo, hi, 29) & 0x55555555u;
+        hi ^= (hi >> 29) & 0x55555555u;
+        // y ^= (y << 17) & b
+        const uint32_t th = __funnelshift_l(lo, hi, 17);
+        lo ^= (lo * k.p17) & 0xEDA60000u;
+        hi ^= th & 0x71D67FFFu;
+        // y ^= (y << 37) & c: only the high half moves
+        hi ^= (lo * k.p5) & 0xFFF7EEE0u;
+        // y ^= y >> 43: only the low half changes
+        lo ^= hi >> 11;
+        return pack64(lo, hi);
     }
 };
 
@@ -102,10 +135,28 @@ __device__ __forceinline__ double f64_of_53(unsigned long long v)
     return __longlong_as_double(static_cast<long long>(bits));
 }
 
-__device__ __forceinline__ double f64_of_u64(unsigned long long z) { return f64_of_53(z >> 11); }
+// the same for v = vh * 2^32 + vl (vh < 2^21) on 32-bit halves: when vh != 0
+// (all but a 2^-21 share of the inputs) the leading one is in vh, so one
+// 32-bit leading-zero count, one funnel shift and one shift normalise v, and
+// the exponent 1021 - sh is added to the high half (the leading one at bit 52
+// turns it into 1022 - sh, the exponent of a value in [2^-1-sh, 2^-sh))
+__device__ __forceinline__ double f64_of_hilo(uint32_t vh, uint32_t vl)
+{
+    if (vh == 0u) return f64_of_53(vl);
+    const int sh = __clz(vh) - 11;
+    const uint32_t mh = __funnelshift_l(vl, vh, sh);
+    const uint32_t ml = vl << sh;
+    return __hiloint2double(static_cast<int>(mh + ((1021u - static_cast<uint32_t>(sh)) << 20)), static_cast<int>(ml));
+}
+
+__device__ __forceinline__ double f64_of_u64(unsigned long long z)
+{
+    return f64_of_hilo(hi32(z) >> 11, __funnelshift_r(lo32(z), hi32(z), 11));
+}
+// ((a >> 5) 2^26 + (b >> 6)) 2^-53: v = (a >> 11) 2^32 + (((a >> 5) << 26) | (b >> 6)) mod 2^32
 __device__ __forceinline__ double f64_of_pair(uint32_t a, uint32_t b)
 {
-    return f64_of_53((static_cast<unsigned long long>(a >> 5) << 26) | (b >> 6));
+    return f64_of_hilo(a >> 11, ((a >> 5) << 26) | (b >> 6));
 }
 __device__ __forceinline__ float f32_of_u64(unsigned long long z) { return f32_of_u32(static_cast<uint32_t>(z >> 32)); }
 

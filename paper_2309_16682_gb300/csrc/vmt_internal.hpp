@@ -50,6 +50,9 @@ struct JumpGrid {
     const int* row_deg;
     const int2* chunk_map;
     int chunk_row0;
+    // run-time recurrence of a twisted GFSR (eq. step with user parameters):
+    // x_{k+n} = x_{k+m} ^ (y >> 1) ^ (y odd ? a : 0), y = (x_k & upper) | (x_{k+1} & lower)
+    unsigned tg_m, tg_upper, tg_lower, tg_a;
 };
 
 // Chunks of one long stream: chunk c starts at S word c * chunk_words(...)
@@ -60,15 +63,29 @@ constexpr int kChunkBlocks = 1024;
 constexpr int kChunkRows = 255;
 inline int64_t chunk_words(int variant, int lanes) { return static_cast<int64_t>(kChunkBlocks) * block_words(variant, lanes); }
 
+// jump of twisted GFSR states (n words each, compiled n only): items' src/dst
+// point at the states, the grid carries the recurrence; cta = one CTA per
+// lane-jump (else one warp); cudaErrorNotSupported for an n not compiled
+constexpr int kTgfsrSizes[] = {4, 5, 17};
+cudaError_t launch_tgfsr_jump(int n, bool cta, const JumpItem* items, long long nitems, const JumpGrid& gr,
+                              const uint32_t* polys, cudaStream_t s);
+
 // ragged: generators of one launch may differ in position or length
 cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, bool ragged, cudaStream_t s);
 cudaError_t launch_seed(int variant, long long count, const unsigned long long* seeds, void* base, cudaStream_t s);
-cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s);
-cudaError_t launch_jump_grid(int variant, const JumpGrid& gr, long long nitems, const uint32_t* polys, cudaStream_t s);
+// compact: every lane-jump on a four-warp CTA with a ~20 KB ring (fits next to
+// running generation CTAs; the server's initialisation), whatever the count
+cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s,
+                        bool compact = false);
+cudaError_t launch_jump_grid(int variant, const JumpGrid& gr, long long nitems, const uint32_t* polys, cudaStream_t s,
+                             bool compact = false);
 cudaError_t launch_fill_int(int* p, long long n, int value, cudaStream_t s);
 // jump launches of fewer items than `items` run one CTA per item
 void set_jump_split_below(int variant, long long items);
 long long get_jump_split_below(int variant);
+// every jump launch of the variant in the compact CTA form
+void set_jump_compact(int variant, bool on);
+bool get_jump_compact(int variant);
 
 }  // namespace vmt
 
@@ -93,10 +110,11 @@ struct vmt_state {
 
 namespace vmt {
 
-// one persistent launch over a unit table already on the device; n units of
-// the given kernel, scheduled through counter (zeroed here)
+// one launch over a unit table already on the device; n units of the given
+// kernel, scheduled through counter (zeroed here), longest first.  Persistent
+// (a few CTAs per SM) by default; cta_per_unit gives each unit its own CTA.
 int launch_unit_table(int variant, int lanes, int dtype, const UnitDesc* d_units, int64_t n, int* counter,
-                      void* stream);
+                      void* stream, bool cta_per_unit = false);
 
 // stream-ordered allocation from `pool`, or from the device's default pool
 // when pool is null
@@ -112,7 +130,7 @@ int init_batch_impl(vmt_state** out, int variant, int lanes, int64_t count, cons
 // several objects of one variant: seeding and offsets once, fan-out per object
 int init_multi_impl(vmt_state** outs, int variant, int nsub, const int* lanes, const int64_t* counts,
                     const uint64_t* seeds, const uint64_t* jumps, void* cuda_stream, bool async_alloc,
-                    cudaMemPool_t pool = nullptr);
+                    cudaMemPool_t pool = nullptr, bool compact_jumps = false);
 void free_state_async(vmt_state* st, void* cuda_stream);
 
 // `count` generators with unset states (to be written by a jump), fresh
@@ -122,10 +140,12 @@ int alloc_states_async(vmt_state** out, int variant, int lanes, int64_t count, v
 
 // chunk states: chunk k = row (chunk_map[k].y) applied to every lane of
 // request chunk_map[k].x of `requests`; d_map on the device
-int launch_chunk_jumps(const vmt_state* requests, vmt_state* chunks, const int2* d_map, void* cuda_stream);
+int launch_chunk_jumps(const vmt_state* requests, vmt_state* chunks, const int2* d_map, void* cuda_stream,
+                       bool compact_jumps = false);
 
-// tuned CTA size for a (variant, lanes) pair (0: the kernel's default)
-int tuned_threads(int variant, int lanes);
+// tuned kernel configuration of a (variant, lanes) pair: an index into that
+// pair's rows of kKernelCfgs (0: the default)
+int tuned_kcfg(int variant, int lanes);
 
 // 1 if a generation kernel gave up on a bounded wait (and reset the flag when asked)
 int read_generate_timeout(bool reset);

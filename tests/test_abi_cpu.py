@@ -147,3 +147,34 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.strip() == "ok"
+
+
+def test_kernel_configuration_table_lists_selects_and_round_trips(L, tmp_path):
+    import paper_2309_16682_gb300 as vmt
+    for variant, lanes in [("mt32", 16), ("mt32", 8), ("mt32", 4), ("mt64", 16), ("mt64", 8), ("mt64", 4)]:
+        cands = vmt.tune_kernels(variant, lanes)
+        assert len(cands) >= 2 and {c["form"] for c in cands} == {"phase", "chain"}
+        for c in cands:
+            assert lanes % c["lanes_per_cta"] == 0 and c["store_bytes"] in (8, 16) and c["threads"] % 32 == 0
+            # a lane group's row is whole 16-byte vectors
+            assert c["lanes_per_cta"] * (8 if variant == "mt64" else 4) >= 16
+    assert vmt.tune_kernels("sfmt", 4) == []
+    old = vmt.tune_get_kernel("mt64", 8)
+    try:
+        n = len(vmt.tune_kernels("mt64", 8))
+        vmt.tune_set_kernel("mt64", 8, n - 1)
+        assert vmt.tune_get_kernel("mt64", 8) == n - 1
+        f = tmp_path / "tune6.txt"
+        vmt.tune_save(f)
+        assert len(f.read_text().split("\n")[1].split()) == 6
+        vmt.tune_set_kernel("mt64", 8, 0)
+        vmt.tune_load(f)
+        assert vmt.tune_get_kernel("mt64", 8) == n - 1
+        with pytest.raises(vmt.VMTError):
+            vmt.tune_set_kernel("mt64", 8, n)
+        bad = tmp_path / "bad6.txt"
+        bad.write_text("1 8 1 3 160 16\n")     # three lanes per CTA: not compiled
+        with pytest.raises(vmt.VMTError):
+            vmt.tune_load(bad)
+    finally:
+        vmt.tune_set_kernel("mt64", 8, old)

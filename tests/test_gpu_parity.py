@@ -323,16 +323,19 @@ def test_batch_and_graph_match_plain_calls(vmt):
 
 @pytest.fixture
 def jump_kernel_mode(vmt, request):
-    """Force every jump launch onto one kernel: 'split' (one CTA per
-    lane-jump) or 'warp' (one warp per lane-jump)."""
+    """Force every jump launch onto one kernel: 'split' (one sixteen-warp CTA
+    per lane-jump), 'compact' (one four-warp CTA per lane-jump over a small
+    ring) or 'warp' (one warp per lane-jump)."""
     value = 1 << 40 if request.param == "split" else 0
     old = {v: vmt.tune_jump(v, value) for v in ("mt32", "mt64", "sfmt")}
+    oldc = {v: vmt.tune_jump_compact(v, request.param == "compact") for v in ("mt32", "mt64", "sfmt")}
     yield request.param
     for v, x in old.items():
         vmt.tune_jump(v, x)
+        vmt.tune_jump_compact(v, oldc[v])
 
 
-@pytest.mark.parametrize("jump_kernel_mode", ["split", "warp"], indirect=True)
+@pytest.mark.parametrize("jump_kernel_mode", ["split", "compact", "warp"], indirect=True)
 @pytest.mark.parametrize("variant", [O.MT32, O.MT64, O.SFMT])
 def test_both_jump_kernels_match_oracle(vmt, oracle_polys, variant, jump_kernel_mode):
     """Seeding, 64-bit offsets (all eight base-256 digits), lane fan-out and a
@@ -409,15 +412,19 @@ def test_every_jump_from_1_to_4096_equals_stepping(vmt, oracle_polys, variant):
     assert np.array_equal(got, base[idx])
 
 
-def test_autotuner_picks_a_compiled_size_and_keeps_results_exact(vmt):
-    old = vmt.tune_get("mt32", 16)
+def test_autotuner_searches_every_configuration_and_keeps_results_exact(vmt):
+    old = vmt.tune_get_kernel("mt32", 16)
+    cands = vmt.tune_kernels("mt32", 16)
     try:
+        best, times = vmt.autotune_grid("mt32", 16, 512, [(3000, "u32"), (3000, "f32")], reps=2)
+        assert len(times) == len(cands) and all(t > 0 for t in times)
+        assert vmt.tune_get_kernel("mt32", 16) == best and times[best] == min(times)
         t, ms = vmt.autotune("mt32", 16, 512, 0, reps=2, segments=[(3000, "u32"), (3000, "f32")])
-        assert t in (512, 1024) and ms > 0 and vmt.tune_get("mt32", 16) == t
+        assert t in {c["threads"] for c in cands} and ms > 0
         seeds = I.splitmix64(11, 4)
         a = _np(vmt.VGenerator("mt32", 16, seeds).generate(5000, "u32"))
-        vmt.tune_set("mt32", 16, 1024 if t == 512 else 512)
+        vmt.tune_set_kernel("mt32", 16, (vmt.tune_get_kernel("mt32", 16) + 1) % len(cands))
         b = _np(vmt.VGenerator("mt32", 16, seeds).generate(5000, "u32"))
         assert np.array_equal(a, b)
     finally:
-        vmt.tune_set("mt32", 16, old if old in (512, 1024) else 0)
+        vmt.tune_set_kernel("mt32", 16, old)
