@@ -414,6 +414,19 @@ class Generation:
     def step(self):
         self.g.generate_multi(self.segs, outs=self.outs)
 
+    def autotune(self, reps: int = 3):
+        """Time every compiled kernel configuration of this workload's
+        (variant, lanes) on its own generator count and output mix, keep the
+        fastest; returns the grid searched with each point's time."""
+        v, m = self.w["variant"], self.w["lanes"]
+        cands = self.vmt.tune_kernels(v, m)
+        if len(cands) < 2:
+            return None
+        best, times = self.vmt.autotune_grid(v, m, self.count, self.segs, reps=reps)
+        return {"best": best, "grid": [dict(c, ms=t) for c, t in zip(cands, times)],
+                "note": "each point: mean of %d calls of the workload's step after a warm-up, better of two "
+                        "alternating rounds; the timed steps use the best" % reps}
+
     def time_steps(self, steps: int, warmup: int, world: int, clk=None):
         """Warm-up, then `steps` timed steps between CUDA events on the
         launching stream; returns (total ms over ranks, per-step ms)."""
@@ -457,7 +470,7 @@ class Generation:
 
 
 def run_extra_config(vmt, workload: str, steps: int, warmup: int, world: int, rank: int, peak, peak_kind,
-                     write_peak):
+                     write_peak, tune: bool = True):
     """The other generation workloads, timed the same way as the headline
     (every rank runs its own slice of the workload's generators)."""
     from paper_2309_16682_gb300 import shard
@@ -465,6 +478,7 @@ def run_extra_config(vmt, workload: str, steps: int, warmup: int, world: int, ra
     count = w["generators"]
     seeds = shard.rank_seeds(workload, world, rank, count)
     job = Generation(vmt, workload, seeds, count)
+    tuned = job.autotune() if tune else None
     total_ms, per_step, _ = job.time_steps(steps, warmup, world)
     launch_ms = float(np.mean(per_step))
     res = {"workload": workload, "variant": w["variant"], "lanes": w["lanes"], "generators_per_gpu": count,
@@ -473,7 +487,7 @@ def run_extra_config(vmt, workload: str, steps: int, warmup: int, world: int, ra
            "unit": UNIT,
            "words_per_s": sum(n * count for n, _ in job.segs) * steps * world / (total_ms / 1e3),
            "step_ms": {"best": float(np.min(per_step)), "median": float(np.median(per_step))},
-           "init_s": job.init_s}
+           "init_s": job.init_s, "tuning": tuned}
     if count > 1:
         res["roofline"] = job.roofline(launch_ms, peak, peak_kind, write_peak)
         if job.out_bytes < (1 << 30):
@@ -502,13 +516,16 @@ def run_gb300(args, world, rank, local):
     job = Generation(vmt, args.workload, seeds, count)
     g, segs, outs, out_bytes = job.g, job.segs, job.outs, job.out_bytes
     init_s = job.init_s
-    tuned = None
-    if args.tune:
-        # the autotuner times each compiled CTA size on this workload: its size
-        # and its fused output mix (both change which size wins)
-        tuned = vmt.autotune(w["variant"], w["lanes"], count, 0, reps=3, segments=segs)
+    # the autotuner times every compiled kernel configuration on this
+    # workload: its generator count and its fused output mix (both change
+    # which configuration wins)
+    if args.kernel >= 0:
+        vmt.tune_set_kernel(w["variant"], w["lanes"], args.kernel)   # a fixed configuration (profiling)
+    tuned = None if (args.no_tune or args.kernel >= 0) else job.autotune()
+    if tuned is not None and args.save_tune:
         vmt.tune_save(vmt.tune_cache_path())   # kept per GPU model; vmt.tune_load reapplies it
-    tune_threads = vmt.tune_get(w["variant"], w["lanes"])
+    tune_kernel = vmt.tune_kernels(w["variant"], w["lanes"])[vmt.tune_get_kernel(w["variant"], w["lanes"])] \
+        if w["variant"] != "sfmt" else None
 
     # the HBM write ceiling of this GPU (store-only kernel), untimed
     write_peak = vmt.measure_store_bw(8 << 30, 5)
@@ -536,12 +553,14 @@ def run_gb300(args, world, rank, local):
         # the bound: a plain device-to-host copy of the same bytes into the same
         # pinned buffers, timed right after (the host's memory is shared with
         # other jobs, so this ceiling moves from run to run)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        for hb, ob in zip(hosts, outs):
-            hb.copy_(ob, non_blocking=True)
-        torch.cuda.synchronize()
-        copy_gbs = out_bytes / (time.perf_counter() - t1) / 1e9
+        copy_gbs = 0.0
+        for _ in range(3):   # best of three: the host's memory is shared with other jobs
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            for hb, ob in zip(hosts, outs):
+                hb.copy_(ob, non_blocking=True)
+            torch.cuda.synchronize()
+            copy_gbs = max(copy_gbs, out_bytes / (time.perf_counter() - t1) / 1e9)
         e2e_val = out_bytes * e2e_steps * world / e2e_s / 1e9
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": out_bytes, "steps": e2e_steps,
@@ -633,7 +652,7 @@ def run_gb300(args, world, rank, local):
         configs = {}
         for name in [n for n in I.WORKLOADS if n != args.workload]:
             configs[name] = run_extra_config(vmt, name, args.config_steps, args.warmup, world, rank, peak,
-                                             peak_kind, write_peak)
+                                             peak_kind, write_peak, tune=not args.no_tune)
             torch.cuda.empty_cache()
 
     served = None
@@ -666,7 +685,7 @@ def run_gb300(args, world, rank, local):
             "step_ms": {"best": float(np.min(per_step)), "median": float(np.median(per_step)),
                         "mean": float(np.mean(per_step))},
             "gpu_launches": args.steps,
-            "tuning": {"threads": tune_threads, "autotune": tuned},
+            "tuning": {"kernel": tune_kernel, "autotune": tuned},
             "e2e": e2e,
             "configs": configs,
             "cpu_baseline": cpu,
@@ -690,7 +709,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="vmt32_m16_g65536", choices=sorted(I.WORKLOADS))
     ap.add_argument("--ref-seconds", type=float, default=12.0)
-    ap.add_argument("--tune", action="store_true", help="run the autotuner before timing")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (time the table's current choice)")
+    ap.add_argument("--save-tune", action="store_true", help="keep the autotuner's table in the per-GPU cache file")
+    ap.add_argument("--kernel", type=int, default=-1,
+                    help="time this kernel configuration index of the workload (no autotuner; for profiling)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-mix measurement")
     ap.add_argument("--no-jump", action="store_true", help="skip the full-size jump measurement")
     ap.add_argument("--no-stream", action="store_true", help="skip the single-stream measurement")
