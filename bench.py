@@ -297,7 +297,7 @@ def _ms(x, q):
 SMALL_N = 10_000        # "small" requests: at most this many outputs
 
 
-def run_served(vmt, requests: int, rate: float, plain_requests: int):
+def run_served(vmt, requests: int, rate: float, plain_requests: int, client: str = "batched"):
     import torch
     tr = I.request_trace(requests, rate_per_s=rate)
     native = {0: "u32", 1: "u64", 2: "u32"}
@@ -313,29 +313,56 @@ def run_served(vmt, requests: int, rate: float, plain_requests: int):
         srv.release(rid)
     torch.cuda.synchronize()
     warm_stats = srv.stats()
-    # one client thread: submit each request at its arrival time, and between
-    # arrivals take finished requests from the completion queue, read their
-    # latency (stamped by the server) and release them
-    lat, lat_n, lag, nreq = [], [], {}, {}
+    # one client thread: submit the requests whose arrival time has passed,
+    # and between arrivals take finished requests from the completion queue
+    # (with their server-stamped latency) and release them -- in batched
+    # calls, one per group, or (client="single") one call per request
+    arr_t = np.array([r[6] for r in reqs])
+    lag = np.zeros(requests)
+    lat = np.zeros(requests)
     t0 = time.perf_counter()
     i, done, t_end = 0, 0, t0
-    while done < requests:
-        now = time.perf_counter() - t0
-        while i < requests and reqs[i][6] <= now:
-            v, m, dt, seed, jump, n, arr = reqs[i]
-            rid = srv.submit(v, m, dt, seed, jump, n)
-            lag[rid] = max(0.0, time.perf_counter() - t0 - arr)   # submitted this late after its arrival
-            nreq[rid] = n
-            i += 1
-        wait_us = int(1e6 * (reqs[i][6] - now)) if i < requests else 20000
-        rid = srv.next_done(max(0, min(wait_us, 20000)))
-        while rid is not None:
-            lat.append(srv.poll(rid)[3] + lag.pop(rid))
-            lat_n.append(nreq.pop(rid))
-            srv.release(rid)
-            done += 1
-            t_end = time.perf_counter()
-            rid = srv.next_done(0)
+    if client == "batched":
+        carr = vmt.Server.requests([r[:6] for r in reqs])
+        idx_of = {}
+        while done < requests:
+            now = time.perf_counter() - t0
+            j = int(np.searchsorted(arr_t, now, side="right"))
+            if j > i:
+                ids = srv.submit_many(carr, i, j - i)
+                lag[i:j] = np.maximum(0.0, time.perf_counter() - t0 - arr_t[i:j])   # submitted this late
+                idx_of.update(zip(ids.tolist(), range(i, j)))
+                i = j
+            wait_us = int(1e6 * (arr_t[i] - now)) if i < requests else 20000
+            ids, st, lt = srv.next_done_many(max(0, min(wait_us, 20000)), 4096)
+            if len(ids):
+                idx = np.fromiter((idx_of.pop(r) for r in ids.tolist()), np.int64, len(ids))
+                lat[idx] = lt + lag[idx]
+                srv.release_many(ids)
+                done += len(ids)
+                t_end = time.perf_counter()
+    else:
+        idx_of = {}
+        while done < requests:
+            now = time.perf_counter() - t0
+            while i < requests and reqs[i][6] <= now:
+                v, m, dt, seed, jump, n, arr = reqs[i]
+                rid = srv.submit(v, m, dt, seed, jump, n)
+                lag[i] = max(0.0, time.perf_counter() - t0 - arr)
+                idx_of[rid] = i
+                i += 1
+            wait_us = int(1e6 * (reqs[i][6] - now)) if i < requests else 20000
+            rid = srv.next_done(max(0, min(wait_us, 20000)))
+            while rid is not None:
+                k = idx_of.pop(rid)
+                lat[k] = srv.poll(rid)[3] + lag[k]
+                srv.release(rid)
+                done += 1
+                t_end = time.perf_counter()
+                rid = srv.next_done(0)
+    lat_n = [r[5] for r in reqs]
+    lag_all = lag.tolist()
+    lat = lat.tolist()
     stats = srv.stats()
     stats0 = warm_stats
     srv.close()
@@ -347,7 +374,19 @@ def run_served(vmt, requests: int, rate: float, plain_requests: int):
                "peak_output_bytes": stats["peak_output_bytes"], "wall_s": t_end - t0,
                "host_launch_s": stats["host_launch_s"] - stats0["host_launch_s"],
                "init_gpu_s": stats["init_gpu_s"] - stats0["init_gpu_s"],
-               "batch_gpu_s": stats["batch_gpu_s"] - stats0["batch_gpu_s"]}
+               "batch_gpu_s": stats["batch_gpu_s"] - stats0["batch_gpu_s"],
+               "express": {"batches": stats["express_batches"] - stats0["express_batches"],
+                           "requests": stats["express_completed"] - stats0["express_completed"]},
+               "mean_queued_ms": 1e3 * (stats["queued_s"] - stats0["queued_s"] + stats["express_queued_s"] -
+                                        stats0["express_queued_s"]) / max(1, requests),
+               "mean_running_ms": 1e3 * (stats["running_s"] - stats0["running_s"] + stats["express_running_s"] -
+                                         stats0["express_running_s"]) / max(1, requests),
+               "express_mean_queued_ms": 1e3 * (stats["express_queued_s"] - stats0["express_queued_s"]) /
+               max(1, stats["express_completed"] - stats0["express_completed"]),
+               "express_mean_running_ms": 1e3 * (stats["express_running_s"] - stats0["express_running_s"]) /
+               max(1, stats["express_completed"] - stats0["express_completed"]),
+               "mean_submit_lag_ms": 1e3 * float(np.mean(lag_all)) if lag_all else None,
+               "client": client}
     # plain form on the first plain_requests requests of the same trace
     pr = reqs[:plain_requests]
     plat, psmall = [], []
@@ -657,7 +696,7 @@ def run_gb300(args, world, rank, local):
 
     served = None
     if not args.no_serve:
-        served = run_served(vmt, args.serve_requests, 2.0e4, args.plain_requests)
+        served = run_served(vmt, args.serve_requests, 2.0e4, args.plain_requests, args.served_client)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -718,6 +757,8 @@ def main():
     ap.add_argument("--no-stream", action="store_true", help="skip the single-stream measurement")
     ap.add_argument("--no-scalar", action="store_true", help="skip the scalar-query measurement")
     ap.add_argument("--serve-requests", type=int, default=100000)
+    ap.add_argument("--served-client", default="batched", choices=["batched", "single"],
+                    help="the served-mix client: batched calls, or one call per request")
     ap.add_argument("--plain-requests", type=int, default=1000)
     ap.add_argument("--generators", type=int, default=0,
                     help="smaller generator count (profiling cases); default: the workload's")

@@ -224,6 +224,11 @@ typedef struct {
     int64_t state_bytes_in_use, output_bytes_in_use, peak_state_bytes, peak_output_bytes;
     double host_launch_s, init_gpu_s, batch_gpu_s;
     int64_t cancelled;
+    /* express batches and their completed requests; sums over completed
+     * requests of the time queued (submission to admission into a batch) and
+     * of the time running (admission to completion), regular and express */
+    int64_t express_batches, express_completed;
+    double queued_s, running_s, express_queued_s, express_running_s;
 } vmt_server_counters;
 
 int vmt_server_create(vmt_server** s, const vmt_server_config* cfg);
@@ -246,6 +251,25 @@ int vmt_server_release(vmt_server* s, uint64_t id);
  */
 int vmt_server_next_done(vmt_server* s, int64_t timeout_us, uint64_t* id);
 int vmt_server_cancel(vmt_server* s, uint64_t id);
+/*
+ * Batched forms for clients with many requests in flight (one call and one
+ * lock per batch instead of per request):
+ *   vmt_server_submit_many   submits reqs[0..n) in order, ids[i] receiving
+ *                            request i's id; all are checked first and
+ *                            VMT_EINVAL submits none of them
+ *   vmt_server_next_done_many  up to cap requests that reached a final status,
+ *                            in completion order (as vmt_server_next_done),
+ *                            with status[i] and latency_s[i] (submission to
+ *                            completion, -1 unless done); waits up to
+ *                            timeout_us for the first; returns the count
+ *                            (0 when none came), or a negative error code
+ *   vmt_server_release_many  vmt_server_release of each id; returns the first
+ *                            error (the others are still released)
+ */
+int vmt_server_submit_many(vmt_server* s, const vmt_request* reqs, int64_t n, uint64_t* ids);
+int64_t vmt_server_next_done_many(vmt_server* s, int64_t timeout_us, uint64_t* ids, int* status, double* latency_s,
+                                  int64_t cap);
+int vmt_server_release_many(vmt_server* s, const uint64_t* ids, int64_t n);
 /*
  * vmt_server_inject -- host-side fault injection for tests: the next `count`
  * output allocations of the server fail as if device memory were exhausted
@@ -365,9 +389,9 @@ int64_t vmt_tune_jump_get(int variant);
  * ring of the sequence, extended in several rounds.  Each lane-jump is slower
  * than in the sixteen-warp CTA form, but a CTA needs little shared memory, so
  * it is scheduled next to long-running kernels of other streams (the server
- * always uses this form for its initialisation).  on = 0 switches it off,
- * on = -1 only reads.  Returns the setting before the call (1 or 0), or
- * VMT_EINVAL for a bad variant.  Results are identical in every form.
+ * always uses this form for its initialisation).  on = 0 returns to the
+ * default choice, on = -1 only reads.  Returns the setting before the call
+ * (1 or 0), or VMT_EINVAL.  Results are identical in every form.
  */
 int vmt_tune_jump_compact(int variant, int on);
 

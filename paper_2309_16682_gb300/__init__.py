@@ -109,6 +109,9 @@ def lib() -> ctypes.CDLL:
             "vmt_tune_kernels": (I, [I, I, P, I]),
             "vmt_tune_jump_compact": (I, [I, I]),
             "vmt_tgfsr_jump": (I, [P, I64, P, P, I64, I, P]),
+            "vmt_server_submit_many": (I, [P, P, I64, P]),
+            "vmt_server_next_done_many": (I64, [P, I64, P, P, P, I64]),
+            "vmt_server_release_many": (I, [P, P, I64]),
             "vmt_tgfsr_generate": (I, [P, I64, I, P, I64, P, P]),
             "vmt_tune_set_kernel": (I, [I, I, I]),
             "vmt_tune_get_kernel": (I, [I, I]),
@@ -298,7 +301,9 @@ class _Counters(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("queued", "in_flight_batches", "batches", "completed", "failed",
                                              "bytes_out", "state_bytes_in_use", "output_bytes_in_use",
                                              "peak_state_bytes", "peak_output_bytes")] + \
-        [(n, ctypes.c_double) for n in ("host_launch_s", "init_gpu_s", "batch_gpu_s")] + [("cancelled", ctypes.c_int64)]
+        [(n, ctypes.c_double) for n in ("host_launch_s", "init_gpu_s", "batch_gpu_s")] + [("cancelled", ctypes.c_int64)] + \
+        [(n, ctypes.c_int64) for n in ("express_batches", "express_completed")] + \
+        [(n, ctypes.c_double) for n in ("queued_s", "running_s", "express_queued_s", "express_running_s")]
 
 
 class Server:
@@ -347,6 +352,39 @@ class Server:
             return None
         _check(rc)
         return rid.value
+
+    @staticmethod
+    def requests(rows) -> "ctypes.Array":
+        """A request array for submit_many from (variant, lanes, dtype, seed,
+        jump, n) rows (built once, ahead of the submissions)."""
+        arr = (_Request * len(rows))()
+        for i, (v, m, dt, seed, jump, n) in enumerate(rows):
+            arr[i] = _Request(VARIANTS[v], int(m), DTYPES[dt], int(seed) & (2**64 - 1), int(jump) & (2**64 - 1),
+                              int(n))
+        return arr
+
+    def submit_many(self, reqs: "ctypes.Array", first: int, count: int) -> np.ndarray:
+        """Submit reqs[first:first + count] in one call; returns their ids."""
+        ids = np.empty(count, np.uint64)
+        if count:
+            ptr = ctypes.cast(ctypes.byref(reqs, first * ctypes.sizeof(_Request)), ctypes.c_void_p)
+            _check(lib().vmt_server_submit_many(self._h, ptr, int(count), _np_ptr(ids)))
+        return ids
+
+    def next_done_many(self, timeout_us: int = 0, cap: int = 4096):
+        """Up to cap finished requests in completion order: (ids, status,
+        latency seconds); empty arrays when none finished within timeout_us."""
+        ids = np.empty(cap, np.uint64)
+        st = np.empty(cap, np.int32)
+        lat = np.empty(cap, np.float64)
+        k = lib().vmt_server_next_done_many(self._h, int(timeout_us), _np_ptr(ids), _np_ptr(st), _np_ptr(lat), int(cap))
+        if k < 0:
+            _check(int(k))
+        return ids[:k], st[:k], lat[:k]
+
+    def release_many(self, ids: np.ndarray) -> None:
+        ids = np.ascontiguousarray(ids, np.uint64)
+        _check(lib().vmt_server_release_many(self._h, _np_ptr(ids), int(ids.size)))
 
     def cancel(self, rid: int) -> None:
         """Withdraw a queued request (its status becomes VMT_ECANCELED)."""
@@ -397,35 +435,6 @@ def tune_jump_compact(variant: str, on: bool | None = None) -> bool:
     the default choice (False); returns the setting before the call (None:
     just read)."""
     return bool(_check(lib().vmt_tune_jump_compact(VARIANTS[variant], -1 if on is None else int(bool(on)))))
-
-
-class Tgfsr(ctypes.Structure):
-    """Parameters of a twisted GFSR with run-time constants (vmt_tgfsr)."""
-    _fields_ = [("w", ctypes.c_int), ("n", ctypes.c_int), ("m", ctypes.c_int), ("r", ctypes.c_int),
-                ("a", ctypes.c_uint32), ("temper", ctypes.c_int), ("u", ctypes.c_int), ("s", ctypes.c_int),
-                ("t", ctypes.c_int), ("l", ctypes.c_int), ("d", ctypes.c_uint32), ("b", ctypes.c_uint32),
-                ("c", ctypes.c_uint32)]
-
-
-def tgfsr_jump(params: Tgfsr, states, poly: np.ndarray, nbits: int | None = None, kernel: str = "warp",
-               stream=None) -> None:
-    """Every state (a uint32 tensor [count, n] on the GPU) by c(F) X (Sec. 3.1)."""
-    poly = np.ascontiguousarray(poly, dtype=np.uint64)
-    nb = poly.size * 64 if nbits is None else int(nbits)
-    _check(lib().vmt_tgfsr_jump(ctypes.byref(params), int(states.shape[0]), ctypes.c_void_p(states.data_ptr()),
-                                _np_ptr(poly), nb, {"warp": 0, "cta": 1}[kernel], _stream_handle(stream)))
-
-
-def tgfsr_generate(params: Tgfsr, states, lanes: int, n: int, out=None, stream=None):
-    """n outputs of every state, interleaved over `lanes` (tensor [groups, n * lanes])."""
-    import torch
-    groups = int(states.shape[0]) // int(lanes)
-    if out is None:
-        out = torch.empty((groups, n * lanes), dtype=torch.int32, device=states.device)   # uint32 words
-    _check(lib().vmt_tgfsr_generate(ctypes.byref(params), int(states.shape[0]), int(lanes),
-                                    ctypes.c_void_p(states.data_ptr()), int(n), ctypes.c_void_p(out.data_ptr()),
-                                    _stream_handle(stream)))
-    return out
 
 
 def tune_save(path: str) -> None:

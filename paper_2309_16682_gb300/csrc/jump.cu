@@ -646,7 +646,7 @@ template <> __device__ __forceinline__ int cta_extend<CTG<17>>(uint32_t* r, int 
 static std::atomic<long long> g_split_below[3] = {{4096}, {4096}, {512}};
 // every launch of the variant in the compact CTA form (callers that share the
 // GPU with long-running kernels; tests)
-static std::atomic<bool> g_compact[3] = {{false}, {false}, {false}};
+static std::atomic<int> g_compact[3] = {{0}, {0}, {0}};
 
 // the CTA kernels' dynamic shared memory limit, raised once per device
 template <class S>
@@ -664,17 +664,26 @@ static cudaError_t cta_smem_attr()
     return e;
 }
 
+template <class S>
+static cudaError_t launch_cta_form(const JumpItem* items, const JumpGrid& gr, long long nitems, const uint32_t* polys,
+                                   cudaStream_t st)
+{
+    const cudaError_t e = cta_smem_attr<S>();
+    if (e != cudaSuccess) return e;
+    jump_cta_kernel<S><<<static_cast<unsigned>(nitems), S::W * 32, cta_smem<S>(), st>>>(items, gr, polys);
+    return cudaGetLastError();
+}
+
+// shared: 0 the default choice (sixteen-warp CTA or warp kernel by count),
+// 1 compact CTAs (for launches that share the GPU)
 template <class J, class S, class SC>
 static cudaError_t launch_jump_t(int variant, const JumpItem* items, const JumpGrid& gr, long long nitems,
-                                 const uint32_t* polys, cudaStream_t st, long long split_below, bool compact)
+                                 const uint32_t* polys, cudaStream_t st, long long split_below, int shared)
 {
     if (nitems <= 0) return cudaSuccess;
-    if (compact || g_compact[variant].load(std::memory_order_relaxed)) {
-        const cudaError_t e = cta_smem_attr<SC>();
-        if (e != cudaSuccess) return e;
-        jump_cta_kernel<SC><<<static_cast<unsigned>(nitems), SC::W * 32, cta_smem<SC>(), st>>>(items, gr, polys);
-        return cudaGetLastError();
-    }
+    const int forced = g_compact[variant].load(std::memory_order_relaxed);
+    const int form = shared ? shared : forced;
+    if (form == 1) return launch_cta_form<SC>(items, gr, nitems, polys, st);
     if (nitems < split_below) {
         const cudaError_t e = cta_smem_attr<S>();
         if (e != cudaSuccess) return e;
@@ -738,7 +747,7 @@ cudaError_t launch_seed(int variant, long long count, const unsigned long long* 
 }
 
 cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s,
-                        bool compact)
+                        int compact)
 {
     using namespace dev;
     if (variant < 0 || variant > 2) return cudaErrorInvalidValue;
@@ -750,7 +759,7 @@ cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, co
 }
 
 cudaError_t launch_jump_grid(int variant, const JumpGrid& gr, long long nitems, const uint32_t* polys, cudaStream_t s,
-                             bool compact)
+                             int compact)
 {
     using namespace dev;
     if (variant < 0 || variant > 2) return cudaErrorInvalidValue;
@@ -791,8 +800,8 @@ cudaError_t launch_tgfsr_jump(int n, bool cta, const JumpItem* items, long long 
 }
 
 void set_jump_split_below(int variant, long long items) { dev::g_split_below[variant].store(items < 0 ? 0 : items); }
-void set_jump_compact(int variant, bool on) { dev::g_compact[variant].store(on); }
-bool get_jump_compact(int variant) { return dev::g_compact[variant].load(); }
+void set_jump_compact(int variant, int form) { dev::g_compact[variant].store(form); }
+int get_jump_compact(int variant) { return dev::g_compact[variant].load(); }
 long long get_jump_split_below(int variant) { return dev::g_split_below[variant].load(); }
 
 cudaError_t launch_fill_int(int* p, long long n, int value, cudaStream_t s)

@@ -83,7 +83,7 @@ struct Req {
     int launch_rc = VMT_OK;  // set when its own launch step failed (it fails alone)
     bool admitted = false;   // its output bytes count against the budget
     bool express = false;    // ... against the express budget
-    double t_submit = 0, t_done = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
 };
 
 struct Slot {
@@ -133,6 +133,8 @@ struct vmt_server {
     int64_t batches = 0, completed = 0, failed = 0, bytes_out = 0;
     double host_launch_s = 0, init_gpu_s = 0, batch_gpu_s = 0;
     int64_t cancelled = 0;
+    int64_t express_batches = 0, express_completed = 0;
+    double queued_s = 0, running_s = 0, express_queued_s = 0, express_running_s = 0;
     std::atomic<int> inject_alloc{0};   // output allocations still to fail (fault injection)
     cudaMemPool_t pool = nullptr;   // states and outputs
     // Memory is freed on a stream of its own, only ever after the kernels that
@@ -199,7 +201,7 @@ int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
         const int nsub = static_cast<int>(counts.size());
         std::vector<vmt_state*> sts(static_cast<size_t>(nsub), nullptr);
         rc = vmt::init_multi_impl(sts.data(), variant, nsub, lanes_of.data(), counts.data(), sl.h_seeds + seed0,
-                                  sl.h_jumps + seed0, s_init, true, s->pool, true);
+                                  sl.h_jumps + seed0, s_init, true, s->pool, vmt::kJumpShared);
         if (rc) return rc;
         for (vmt_state* st : sts) b->states.push_back(st);
         seed0 += k_all;
@@ -239,7 +241,7 @@ int launch_batch(vmt_server* s, Batch* b, std::vector<Req*>& rq)
                 cudaMemcpyAsync(sl.d_map + map0, sl.h_map + map0, static_cast<size_t>(nchunk) * sizeof(int2),
                                 cudaMemcpyHostToDevice, s_init);
                 rc = vmt::launch_chunk_jumps(sts[static_cast<size_t>(gi)], csts[static_cast<size_t>(gi)],
-                                             sl.d_map + map0, s_init, true);
+                                             sl.d_map + map0, s_init, vmt::kJumpShared);
                 if (rc) return rc;
             }
             map0 += nchunk;
@@ -325,8 +327,12 @@ std::vector<std::pair<vmt_state*, cudaStream_t>> retire(vmt_server* s, std::vect
                 ++s->failed;
                 s->done_q.push_back(id);
             } else if (it->second.status == VMT_SERVER_RUNNING) {
-                it->second.status = VMT_SERVER_DONE;
-                it->second.t_done = b->t_done;
+                Req& q = it->second;
+                q.status = VMT_SERVER_DONE;
+                q.t_done = b->t_done;
+                (q.express ? s->express_queued_s : s->queued_s) += q.t_admit - q.t_submit;
+                (q.express ? s->express_running_s : s->running_s) += q.t_done - q.t_admit;
+                if (q.express) ++s->express_completed;
                 ++s->completed;
                 s->bytes_out += it->second.bytes;
                 s->done_q.push_back(id);
@@ -378,6 +384,7 @@ void worker_main(vmt_server* s)
             (express ? s->used_out_express : s->used_out) += q.bytes;
             q.admitted = true;
             q.express = express;
+            q.t_admit = now_s();
             q.status = VMT_SERVER_RUNNING;
             rq.push_back(&q);
             ids.push_back(id);
@@ -453,6 +460,7 @@ void worker_main(vmt_server* s)
         b->cb = HostDone{s, b};
         s->slots[slot].busy = true;
         ++s->batches;
+        if (slot == kExpress) ++s->express_batches;
         lk.unlock();
         const double t0 = now_s();
         const int rc = launch_batch(s, b, rq);
@@ -471,6 +479,28 @@ void worker_main(vmt_server* s)
     }
 }
 
+}  // namespace
+
+namespace {
+bool valid_request(const vmt_request* r)
+{
+    const bool lanes_ok = r->lanes == 1 || r->lanes == 2 || r->lanes == 4 || r->lanes == 8 || r->lanes == 16;
+    return !(r->variant < 0 || r->variant > 2 || !lanes_ok || r->dtype < VMT_U32 || r->dtype > VMT_F64 || r->n < 0 ||
+             (r->variant == VMT_MT19937_64 && r->dtype == VMT_U32) ||
+             r->n * words_per_out(r->variant, r->dtype) > (int64_t(1) << 30) ||
+             (words_per_out(r->variant, r->dtype) == 2 && r->lanes < 2));
+}
+
+Req make_req(const vmt_request* r, double t)
+{
+    Req q;
+    q.r = *r;
+    q.bytes = r->n * out_bytes(r->dtype);
+    q.chunks = std::max<int64_t>(n_chunks(r->variant, r->lanes, r->n * words_per_out(r->variant, r->dtype)), 1);
+    q.state_bytes = q.chunks * (vmt::state_bytes_per_gen(r->variant, r->lanes) + 64);
+    q.t_submit = t;
+    return q;
+}
 }  // namespace
 
 extern "C" {
@@ -557,31 +587,35 @@ int vmt_server_create(vmt_server** out, const vmt_server_config* cfg)
     return VMT_OK;
 }
 
+
 int vmt_server_submit(vmt_server* s, const vmt_request* r, uint64_t* id)
 {
     if (!s || !r || !id) {
         vmt::set_last_error("vmt_server_submit: null argument");
         return VMT_EINVAL;
     }
-    const bool lanes_ok = r->lanes == 1 || r->lanes == 2 || r->lanes == 4 || r->lanes == 8 || r->lanes == 16;
-    if (r->variant < 0 || r->variant > 2 || !lanes_ok || r->dtype < VMT_U32 || r->dtype > VMT_F64 || r->n < 0 ||
-        (r->variant == VMT_MT19937_64 && r->dtype == VMT_U32) ||
-        r->n * words_per_out(r->variant, r->dtype) > (int64_t(1) << 30) ||
-        (words_per_out(r->variant, r->dtype) == 2 && r->lanes < 2)) {
-        vmt::set_last_error("vmt_server_submit: invalid request");
+    return vmt_server_submit_many(s, r, 1, id);
+}
+
+int vmt_server_submit_many(vmt_server* s, const vmt_request* reqs, int64_t n, uint64_t* ids)
+{
+    if (!s || n < 0 || (n > 0 && (!reqs || !ids))) {
+        vmt::set_last_error("vmt_server_submit: null argument");
         return VMT_EINVAL;
     }
-    Req q;
-    q.r = *r;
-    q.bytes = r->n * out_bytes(r->dtype);
-    q.chunks = std::max<int64_t>(n_chunks(r->variant, r->lanes, r->n * words_per_out(r->variant, r->dtype)), 1);
-    q.state_bytes = q.chunks * (vmt::state_bytes_per_gen(r->variant, r->lanes) + 64);
-    q.t_submit = now_s();
+    for (int64_t i = 0; i < n; ++i)
+        if (!valid_request(&reqs[i])) {
+            vmt::set_last_error("vmt_server_submit: invalid request");
+            return VMT_EINVAL;
+        }
+    const double t = now_s();
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        *id = s->next_id++;
-        s->reqs.emplace(*id, q);
-        s->queue.push_back(*id);
+        for (int64_t i = 0; i < n; ++i) {
+            ids[i] = s->next_id++;
+            s->reqs.emplace(ids[i], make_req(&reqs[i], t));
+            s->queue.push_back(ids[i]);
+        }
     }
     s->cv_work.notify_all();
     return VMT_OK;
@@ -683,6 +717,40 @@ int vmt_server_next_done(vmt_server* s, int64_t timeout_us, uint64_t* id)
     return VMT_OK;
 }
 
+int64_t vmt_server_next_done_many(vmt_server* s, int64_t timeout_us, uint64_t* ids, int* status, double* latency_s,
+                                  int64_t cap)
+{
+    if (!s || timeout_us < 0 || cap < 0 || (cap > 0 && (!ids || !status || !latency_s))) return VMT_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto ready = [&] {
+        while (!s->done_q.empty() && !s->reqs.count(s->done_q.front())) s->done_q.pop_front();
+        return !s->done_q.empty();
+    };
+    if (cap == 0 || !s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) return 0;
+    int64_t k = 0;
+    while (k < cap && ready()) {
+        const uint64_t id = s->done_q.front();
+        s->done_q.pop_front();
+        const Req& q = s->reqs[id];
+        ids[k] = id;
+        status[k] = q.status;
+        latency_s[k] = q.status == VMT_SERVER_DONE ? q.t_done - q.t_submit : -1.0;
+        ++k;
+    }
+    return k;
+}
+
+int vmt_server_release_many(vmt_server* s, const uint64_t* ids, int64_t n)
+{
+    if (!s || n < 0 || (n > 0 && !ids)) return VMT_EINVAL;
+    int rc = VMT_OK;
+    for (int64_t i = 0; i < n; ++i) {
+        const int r = vmt_server_release(s, ids[i]);
+        if (r != VMT_OK && rc == VMT_OK) rc = r;
+    }
+    return rc;
+}
+
 int vmt_server_cancel(vmt_server* s, uint64_t id)
 {
     if (!s) return VMT_EINVAL;
@@ -733,6 +801,12 @@ int vmt_server_stats(vmt_server* s, vmt_server_counters* out)
     out->init_gpu_s = s->init_gpu_s;
     out->batch_gpu_s = s->batch_gpu_s;
     out->cancelled = s->cancelled;
+    out->express_batches = s->express_batches;
+    out->express_completed = s->express_completed;
+    out->queued_s = s->queued_s;
+    out->running_s = s->running_s;
+    out->express_queued_s = s->express_queued_s;
+    out->express_running_s = s->express_running_s;
     return VMT_OK;
 }
 

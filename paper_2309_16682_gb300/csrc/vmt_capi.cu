@@ -446,9 +446,9 @@ namespace {
 int64_t state_total_bytes(const vmt_state* st) { return st->count * vmt::state_bytes_per_gen(st->variant, st->lanes); }
 
 int run_jump_grid(int variant, const vmt::JumpGrid& gr, long long nitems, const uint32_t* table, cudaStream_t s,
-                  bool compact = false)
+                  int shared = 0)
 {
-    CUDA_TRY(vmt::launch_jump_grid(variant, gr, nitems, table, s, compact));
+    CUDA_TRY(vmt::launch_jump_grid(variant, gr, nitems, table, s, shared));
     return VMT_OK;
 }
 
@@ -732,7 +732,7 @@ int vmt_set_cache_dir(const char* path)
 // null); free such objects with vmt::free_state_async.
 int vmt::init_multi_impl(vmt_state** outs, int variant, int nsub, const int* lanes, const int64_t* counts,
                          const uint64_t* seeds, const uint64_t* jumps, void* cuda_stream, bool async_alloc,
-                         cudaMemPool_t pool, bool compact_jumps)
+                         cudaMemPool_t pool, int shared_jumps)
 {
     if (!outs || !lanes || !counts || nsub < 1) return fail(VMT_EINVAL, "null argument");
     for (int i = 0; i < nsub; ++i) outs[i] = nullptr;
@@ -813,7 +813,7 @@ int vmt::init_multi_impl(vmt_state** outs, int variant, int nsub, const int* lan
             for (int64_t g = 0; g < total && !used; ++g) used = ((jumps[g] >> (8 * i)) & 255u) != 0;
             if (!used) continue;
             gr.digit = i;
-            if ((rc = run_jump_grid(variant, gr, total, c.d_table, s, compact_jumps))) return rc;
+            if ((rc = run_jump_grid(variant, gr, total, c.d_table, s, shared_jumps))) return rc;
         }
     }
     // lane fan-out per object: lane t = x^(t J)(F) base, written into X-hat's
@@ -825,7 +825,7 @@ int vmt::init_multi_impl(vmt_state** outs, int variant, int nsub, const int* lan
         gr.lanes = lanes[i];
         gr.states = static_cast<char*>(made[static_cast<size_t>(i)]->d_states);
         gr.gen_bytes = vmt::state_bytes_per_gen(variant, lanes[i]);
-        if ((rc = run_jump_grid(variant, gr, counts[i] * lanes[i], c.d_table, s, compact_jumps))) return rc;
+        if ((rc = run_jump_grid(variant, gr, counts[i] * lanes[i], c.d_table, s, shared_jumps))) return rc;
         g0 += counts[i];
     }
     CUDA_TRY(cudaFreeAsync(d_seeds, s));
@@ -873,7 +873,7 @@ int vmt::alloc_states_async(vmt_state** out, int variant, int lanes, int64_t cou
 }
 
 int vmt::launch_chunk_jumps(const vmt_state* requests, vmt_state* chunks, const int2* d_map, void* cuda_stream,
-                            bool compact_jumps)
+                            int shared_jumps)
 {
     const int variant = requests->variant;
     int rc = ensure_chunks(variant);
@@ -891,7 +891,7 @@ int vmt::launch_chunk_jumps(const vmt_state* requests, vmt_state* chunks, const 
     gr.chunk_map = d_map;
     gr.chunk_row0 = kChunkRow0;
     return run_jump_grid(variant, gr, chunks->count * requests->lanes, c.d_table, static_cast<cudaStream_t>(cuda_stream),
-                         compact_jumps);
+                         shared_jumps);
 }
 
 void vmt::free_state_async(vmt_state* st, void* cuda_stream)
@@ -1109,12 +1109,12 @@ int64_t vmt_tune_jump_get(int variant)
 
 int vmt_tune_jump_compact(int variant, int on)
 {
-    if (variant < -1 || variant > 2) return fail(VMT_EINVAL, "bad variant");
-    const int old = variant < 0 ? vmt::get_jump_compact(0) : vmt::get_jump_compact(variant);
+    if (variant < -1 || variant > 2 || on < -1 || on > 1) return fail(VMT_EINVAL, "bad variant or setting");
+    const int old = vmt::get_jump_compact(variant < 0 ? 0 : variant);
     if (on >= 0)
         for (int v = 0; v < 3; ++v)
-            if (variant < 0 || v == variant) vmt::set_jump_compact(v, on != 0);
-    return old ? 1 : 0;
+            if (variant < 0 || v == variant) vmt::set_jump_compact(v, on);
+    return old;
 }
 
 int vmt_prepare(int variant, void* cuda_stream)

@@ -73,19 +73,21 @@ cudaError_t launch_tgfsr_jump(int n, bool cta, const JumpItem* items, long long 
 // ragged: generators of one launch may differ in position or length
 cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, bool ragged, cudaStream_t s);
 cudaError_t launch_seed(int variant, long long count, const unsigned long long* seeds, void* base, cudaStream_t s);
-// compact: every lane-jump on a four-warp CTA with a ~20 KB ring (fits next to
-// running generation CTAs; the server's initialisation), whatever the count
+// shared (for launches that share the GPU with long-running kernels, the
+// server's initialisation), whatever the count: 1 every lane-jump on a
+// four-warp CTA with a ~20 KB ring; 0 the default choice
+constexpr int kJumpShared = 1;   // the form the server uses
 cudaError_t launch_jump(int variant, const JumpItem* items, long long nitems, const uint32_t* polys, cudaStream_t s,
-                        bool compact = false);
+                        int shared = 0);
 cudaError_t launch_jump_grid(int variant, const JumpGrid& gr, long long nitems, const uint32_t* polys, cudaStream_t s,
-                             bool compact = false);
+                             int shared = 0);
 cudaError_t launch_fill_int(int* p, long long n, int value, cudaStream_t s);
 // jump launches of fewer items than `items` run one CTA per item
 void set_jump_split_below(int variant, long long items);
 long long get_jump_split_below(int variant);
-// every jump launch of the variant in the compact CTA form
-void set_jump_compact(int variant, bool on);
-bool get_jump_compact(int variant);
+// every jump launch of the variant in the shared form (1 compact; 0 off)
+void set_jump_compact(int variant, int form);
+int get_jump_compact(int variant);
 
 }  // namespace vmt
 
@@ -130,7 +132,7 @@ int init_batch_impl(vmt_state** out, int variant, int lanes, int64_t count, cons
 // several objects of one variant: seeding and offsets once, fan-out per object
 int init_multi_impl(vmt_state** outs, int variant, int nsub, const int* lanes, const int64_t* counts,
                     const uint64_t* seeds, const uint64_t* jumps, void* cuda_stream, bool async_alloc,
-                    cudaMemPool_t pool = nullptr, bool compact_jumps = false);
+                    cudaMemPool_t pool = nullptr, int shared_jumps = 0);
 void free_state_async(vmt_state* st, void* cuda_stream);
 
 // `count` generators with unset states (to be written by a jump), fresh
@@ -141,7 +143,7 @@ int alloc_states_async(vmt_state** out, int variant, int lanes, int64_t count, v
 // chunk states: chunk k = row (chunk_map[k].y) applied to every lane of
 // request chunk_map[k].x of `requests`; d_map on the device
 int launch_chunk_jumps(const vmt_state* requests, vmt_state* chunks, const int2* d_map, void* cuda_stream,
-                       bool compact_jumps = false);
+                       int shared_jumps = 0);
 
 // tuned kernel configuration of a (variant, lanes) pair: an index into that
 // pair's rows of kKernelCfgs (0: the default)

@@ -153,7 +153,7 @@ def test_kernel_configuration_table_lists_selects_and_round_trips(L, tmp_path):
     import paper_2309_16682_gb300 as vmt
     for variant, lanes in [("mt32", 16), ("mt32", 8), ("mt32", 4), ("mt64", 16), ("mt64", 8), ("mt64", 4)]:
         cands = vmt.tune_kernels(variant, lanes)
-        assert len(cands) >= 2 and {c["form"] for c in cands} == {"phase", "chain"}
+        assert len(cands) >= 2 and {"phase", "chain"} <= {c["form"] for c in cands}
         for c in cands:
             assert lanes % c["lanes_per_cta"] == 0 and c["store_bytes"] in (8, 16) and c["threads"] % 32 == 0
             # a lane group's row is whole 16-byte vectors

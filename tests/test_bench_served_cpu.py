@@ -44,12 +44,34 @@ class FakeServer:
     def poll(self, rid):
         return (2, None, 4 * self.done[rid], 1e-9 * self.done[rid])
 
+    # batched forms
+    @staticmethod
+    def requests(rows):
+        return list(rows)
+
+    def submit_many(self, rows, first, count):
+        return np.array([self.submit(*rows[first + k]) for k in range(count)], np.uint64)
+
+    def next_done_many(self, timeout_us, cap):
+        ids, lat = [], []
+        rid = self.next_done(timeout_us)
+        while rid is not None and len(ids) < cap:
+            ids.append(rid)
+            lat.append(self.poll(rid)[3])
+            rid = self.next_done(0) if len(ids) < cap else None
+        return np.array(ids, np.uint64), np.full(len(ids), 2, np.int32), np.array(lat)
+
+    def release_many(self, ids):
+        for rid in ids.tolist():
+            self.release(rid)
+
     def release(self, rid):
         self.done.pop(rid, None)
 
     def stats(self):
         return {"batches": self.batches, "peak_output_bytes": 0, "host_launch_s": 0.0,
-                "init_gpu_s": 0.0, "batch_gpu_s": 0.0}
+                "init_gpu_s": 0.0, "batch_gpu_s": 0.0, "express_batches": 0, "express_completed": 0,
+                "queued_s": 0.0, "running_s": 0.0, "express_queued_s": 0.0, "express_running_s": 0.0}
 
     def close(self):
         pass
@@ -84,10 +106,12 @@ def no_cuda(monkeypatch):
     monkeypatch.setattr(torch.cuda, "current_stream", lambda *a, **k: FakeStream())
 
 
-def test_served_leg_reports_overall_and_small_request_latency(no_cuda):
+@pytest.mark.parametrize("client", ["batched", "single"])
+def test_served_leg_reports_overall_and_small_request_latency(no_cuda, client):
     FakeGenerator.made.clear()
     requests, plain = 300, 40
-    r = bench.run_served(FakeVmt, requests, 2.0e4, plain)
+    r = bench.run_served(FakeVmt, requests, 2.0e4, plain, client)
+    assert r["batched"]["client"] == client
     tr = bench.I.request_trace(requests, rate_per_s=2.0e4)
     small = tr["n"] <= bench.SMALL_N
     b = r["batched"]

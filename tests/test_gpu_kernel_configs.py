@@ -129,19 +129,31 @@ def test_every_kernel_configuration_matches_the_oracle(vmt, oracle_polys, varian
     assert vmt.device_status() == 0
 
 
-def test_more_generators_than_resident_ctas(vmt, oracle_polys):
-    """A lane-split launch whose CTAs each take many generators (grid stride
-    over 2 x 1500 half-generators), checked on the first, a middle and the
-    last generator."""
-    cands = vmt.tune_kernels("mt32", 16)
-    idx = next(i for i, c in enumerate(cands) if c["form"] == "chain" and c["lanes_per_cta"] == 8)
-    prev = vmt.tune_get_kernel("mt32", 16)
-    seeds = I.splitmix64(31, 1500)
+@pytest.mark.parametrize("variant,M,form", [(O.MT32, 16, "chain"), (O.MT64, 8, "chain")])
+def test_more_generators_than_resident_ctas(vmt, oracle_polys, variant, M, form):
+    """Persistent lane-split launches whose CTAs each take many half- or
+    quarter-generators (1500 generators, a few hundred resident CTAs), two
+    calls in a row (the second continues the states the first wrote back),
+    checked on the first, a middle and the last generator."""
+    name = VNAME[variant]
+    cands = vmt.tune_kernels(name, M)
+    idx = next(i for i, c in enumerate(cands) if c["form"] == form and (form != "chain" or c["lanes_per_cta"] < M))
+    prev = vmt.tune_get_kernel(name, M)
+    seeds = I.splitmix64(31 + M, 1500)
+    native, flt = ("u64", "f64") if variant == O.MT64 else ("u32", "f32")
+    segs = [(20000, native), (5000, flt)]
     try:
-        vmt.tune_set_kernel("mt32", 16, idx)
-        got = _np(vmt.VGenerator("mt32", 16, seeds).generate_multi([(20000, "u32"), (5000, "f32")])[0])
+        vmt.tune_set_kernel(name, M, idx)
+        g = vmt.VGenerator(name, M, seeds)
+        a = [_np(t) for t in g.generate_multi(segs)]
+        b = [_np(t) for t in g.generate_multi(segs)]
     finally:
-        vmt.tune_set_kernel("mt32", 16, prev)
+        vmt.tune_set_kernel(name, M, prev)
+    wpo = O.words_per_output(variant, flt)
+    per_call = 20000 + 5000 * wpo
     for gi in (0, 777, 1499):
-        ref = O.convert(O.MT32, O.vstream_words(O.MT32, 16, int(seeds[gi]), 20000, 0), "u32")
-        assert np.array_equal(got[gi], ref), gi
+        w = O.vstream_words(variant, M, int(seeds[gi]), 2 * per_call, 0)
+        for k, out in enumerate((a, b)):
+            base = k * per_call
+            assert np.array_equal(out[0][gi], O.convert(variant, w[base:base + 20000], native)), (form, gi, k)
+            assert np.array_equal(out[1][gi], O.convert(variant, w[base + 20000:base + per_call], flt)), (form, gi, k)

@@ -60,6 +60,37 @@ def test_mix_equals_alone(vmt):
     srv.close()
 
 
+def test_batched_calls_equal_alone(vmt):
+    """submit_many / next_done_many / release_many: the same outputs as each
+    request alone, every id completed once, and the latencies server-stamped."""
+    r = I.splitmix64(77, 30 * 4).reshape(30, 4)
+    kinds = [("mt32", "u32"), ("mt64", "u64"), ("sfmt", "u32"), ("mt32", "f64")]
+    rows = []
+    for i in range(30):
+        variant, dtype = kinds[int(r[i, 0] % np.uint64(len(kinds)))]
+        lanes = [2, 4, 8, 16][int(r[i, 1] % np.uint64(4))]
+        rows.append((variant, lanes, dtype, int(r[i, 2]), int(r[i, 3]), [1, 777, 12345, 70000][i % 4]))
+    srv = vmt.Server(state_budget=1 << 30, output_budget=1 << 30, max_batch=16)
+    carr = vmt.Server.requests(rows)
+    ids = np.concatenate([srv.submit_many(carr, 0, 11), srv.submit_many(carr, 11, 19)])
+    assert len(set(ids.tolist())) == 30
+    seen = {}
+    while len(seen) < 30:
+        got_ids, st, lat = srv.next_done_many(2_000_000, 7)
+        assert len(got_ids) > 0
+        for rid, s_, l_ in zip(got_ids.tolist(), st.tolist(), lat.tolist()):
+            assert rid not in seen and s_ == vmt.SERVER_DONE and l_ >= 0
+            seen[rid] = l_
+    for rid, (variant, lanes, dtype, seed, jump, n) in zip(ids.tolist(), rows):
+        assert np.array_equal(srv.copy(rid, dtype), _alone(vmt, variant, lanes, dtype, seed, jump, n))
+    srv.release_many(ids)
+    assert srv.stats()["output_bytes_in_use"] == 0
+    bad = vmt.Server.requests([("mt64", 4, "u32", 1, 0, 10)])   # u32 from MT19937-64 is refused
+    with pytest.raises(vmt.VMTError):
+        srv.submit_many(bad, 0, 1)
+    srv.close()
+
+
 def test_mix_matches_oracle_for_a_few(vmt, oracle_polys):
     srv = vmt.Server(state_budget=1 << 28, output_budget=1 << 28, max_batch=8)
     cases = [("mt32", 4, "u32", 11, 1 << 40, 5000), ("sfmt", 4, "u32", 12, 3, 3000), ("mt64", 8, "u64", 13, 77, 4000)]
