@@ -437,6 +437,35 @@ def tune_jump_compact(variant: str, on: bool | None = None) -> bool:
     return bool(_check(lib().vmt_tune_jump_compact(VARIANTS[variant], -1 if on is None else int(bool(on)))))
 
 
+class Tgfsr(ctypes.Structure):
+    """Parameters of a twisted GFSR with run-time constants (vmt_tgfsr)."""
+    _fields_ = [("w", ctypes.c_int), ("n", ctypes.c_int), ("m", ctypes.c_int), ("r", ctypes.c_int),
+                ("a", ctypes.c_uint32), ("temper", ctypes.c_int), ("u", ctypes.c_int), ("s", ctypes.c_int),
+                ("t", ctypes.c_int), ("l", ctypes.c_int), ("d", ctypes.c_uint32), ("b", ctypes.c_uint32),
+                ("c", ctypes.c_uint32)]
+
+
+def tgfsr_jump(params: Tgfsr, states, poly: np.ndarray, nbits: int | None = None, kernel: str = "warp",
+               stream=None) -> None:
+    """Every state (a uint32 tensor [count, n] on the GPU) by c(F) X (Sec. 3.1)."""
+    poly = np.ascontiguousarray(poly, dtype=np.uint64)
+    nb = poly.size * 64 if nbits is None else int(nbits)
+    _check(lib().vmt_tgfsr_jump(ctypes.byref(params), int(states.shape[0]), ctypes.c_void_p(states.data_ptr()),
+                                _np_ptr(poly), nb, {"warp": 0, "cta": 1}[kernel], _stream_handle(stream)))
+
+
+def tgfsr_generate(params: Tgfsr, states, lanes: int, n: int, out=None, stream=None):
+    """n outputs of every state, interleaved over `lanes` (tensor [groups, n * lanes])."""
+    import torch
+    groups = int(states.shape[0]) // int(lanes)
+    if out is None:
+        out = torch.empty((groups, n * lanes), dtype=torch.int32, device=states.device)   # uint32 words
+    _check(lib().vmt_tgfsr_generate(ctypes.byref(params), int(states.shape[0]), int(lanes),
+                                    ctypes.c_void_p(states.data_ptr()), int(n), ctypes.c_void_p(out.data_ptr()),
+                                    _stream_handle(stream)))
+    return out
+
+
 def tune_save(path: str) -> None:
     """Write the tuning table (entries that differ from the defaults)."""
     _check(lib().vmt_tune_save(os.fspath(path).encode()))

@@ -73,6 +73,31 @@ __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G
             }
             return;
         }
+        if (plan.ok) {
+            // a phase that holds the end of the call's output or the segment
+            // boundary: a whole vector inside [0, hi) takes the typed store of
+            // its segment (the boundary falls between vectors), the vector
+            // that straddles hi the word path, vectors at or beyond hi only
+            // advance the state
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const int v = V0 + tid + i * T;
+                if (((i + 1) * T <= V1 - V0) || v < V1) {
+                    W z[VW];
+                    twist_item<G, M, VW, K0, K1>(cur, nxt, v, z, em.a.k);
+                    const int f0 = v * VW;
+                    if (f0 + VW <= hi) {
+                        if (P::nseg == 2 && f0 >= plan.b1)
+                            store_typed<(P::nseg == 2 ? P::DT1 : P::DT0), W, VW>(plan.base1, f0, z);
+                        else
+                            store_typed<P::DT0, W, VW>(plan.base0, f0, z);
+                    } else if (f0 < hi) {
+                        emit_words<VW>(em, f0, z, 0, hi, e);
+                    }
+                }
+            }
+            return;
+        }
     }
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -187,14 +212,39 @@ __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(
             // rest of the current block: block word f is call word f - p
             const int hi = min(B, p + total);
             plan.template make<P, W, VW>(a, em, -static_cast<long long>(p));
-            for (int v0 = p / VW; v0 * VW < hi; v0 += T) {
-                const int v = v0 + tid;
-                W w[VW], z[VW];
-                const bool act = v * VW < hi;
-                if (act) ldv<W, VW>(cur + v * VW, w);
+            bool done_head = false;
+            if constexpr (!P::generic) {
+                if (plan.ok) {
+                    // whole vectors inside [p, hi) take the typed store of their
+                    // segment, the ones that straddle p or hi the word path
+                    for (int v = p / VW + tid; v * VW < hi; v += T) {
+                        const int f0 = v * VW;
+                        W w[VW], z[VW];
+                        ldv<W, VW>(cur + f0, w);
 #pragma unroll
-                for (int u = 0; u < VW; ++u) z[u] = act ? G::temper(w[u], a.k) : W(0);
-                emit_p<P, W, VW>(plan, em, v * VW, z, p, hi, -static_cast<long long>(p), act, true);
+                        for (int u = 0; u < VW; ++u) z[u] = G::temper(w[u], a.k);
+                        if (f0 >= p && f0 + VW <= hi) {
+                            if (P::nseg == 2 && f0 >= plan.b1)
+                                store_typed<(P::nseg == 2 ? P::DT1 : P::DT0), W, VW>(plan.base1, f0, z);
+                            else
+                                store_typed<P::DT0, W, VW>(plan.base0, f0, z);
+                        } else {
+                            emit_words<VW>(em, f0, z, p, hi, 0);
+                        }
+                    }
+                    done_head = true;
+                }
+            }
+            if (!done_head) {
+                for (int v0 = p / VW; v0 * VW < hi; v0 += T) {
+                    const int v = v0 + tid;
+                    W w[VW], z[VW];
+                    const bool act = v * VW < hi;
+                    if (act) ldv<W, VW>(cur + v * VW, w);
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) z[u] = act ? G::temper(w[u], a.k) : W(0);
+                    emit_p<P, W, VW>(plan, em, v * VW, z, p, hi, -static_cast<long long>(p), act, true);
+                }
             }
             e = hi - p;
             final_pos = hi;

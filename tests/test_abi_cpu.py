@@ -178,3 +178,16 @@ def test_kernel_configuration_table_lists_selects_and_round_trips(L, tmp_path):
             vmt.tune_load(bad)
     finally:
         vmt.tune_set_kernel("mt64", 8, old)
+
+
+def test_binding_exposes_its_public_calls():
+    """Every Python wrapper of the C ABI is present (CPU; no call is made)."""
+    import paper_2309_16682_gb300 as vmt
+    for name in ["VGenerator", "ScalarGenerator", "Server", "Batch", "Tgfsr", "tgfsr_jump", "tgfsr_generate",
+                 "jump_poly", "stream_generate", "prepare", "measure_store_bw", "device_status", "tune_set",
+                 "tune_get", "tune_kernels", "tune_set_kernel", "tune_get_kernel", "tune_jump", "tune_jump_compact",
+                 "tune_save", "tune_load", "autotune", "autotune_grid", "poly_minpoly", "poly_mulmod", "poly_x2pow"]:
+        assert hasattr(vmt, name), name
+    for name in ["submit", "submit_many", "requests", "next_done", "next_done_many", "release", "release_many",
+                 "poll", "wait", "copy", "cancel", "stats", "close"]:
+        assert hasattr(vmt.Server, name), name
