@@ -22,25 +22,33 @@ namespace dev {
 
 // One item of a twist phase: vector v of the new block from the old block
 // `cur` and the rows of `nxt` finished by earlier phases.
+// the new words of vector v (written to nxt and returned in nw)
 template <class G, int M, int VW, int K0, int K1>
-__device__ __forceinline__ void twist_item(const typename G::W* cur, typename G::W* nxt, int v,
-                                           typename G::W (&z)[VW], const ShiftK& k)
+__device__ __forceinline__ void twist_vec(const typename G::W* cur, typename G::W* nxt, int v,
+                                          typename G::W (&nw)[VW], const ShiftK& k)
 {
     using W = typename G::W;
     constexpr int N = G::N, MM = G::MM, NM = N - MM;
     constexpr int RV = M / VW, NV = N * RV;
-    W xa[VW], xb[VW], xc[VW], nw[VW];
+    W xa[VW], xb[VW], xc[VW];
     ldv<W, VW>(cur + v * VW, xa);
     if (K1 < N || v + RV < NV) ldv<W, VW>(cur + (v + RV) * VW, xb);   // old x_{k+1}
     else ldv<W, VW>(nxt + (v + RV - NV) * VW, xb);                    // new x_0 for the last row
     if (K0 == 0) ldv<W, VW>(cur + (v + MM * RV) * VW, xc);          // old x_{k+m}
     else ldv<W, VW>(nxt + (v - NM * RV) * VW, xc);                  // new x_{k-(n-m)}
 #pragma unroll
-    for (int u = 0; u < VW; ++u) {
-        nw[u] = G::twist(xa[u], xb[u], xc[u], k);
-        z[u] = G::temper(nw[u], k);
-    }
+    for (int u = 0; u < VW; ++u) nw[u] = G::twist(xa[u], xb[u], xc[u], k);
     stv<W, VW>(nxt + v * VW, nw);
+}
+
+template <class G, int M, int VW, int K0, int K1>
+__device__ __forceinline__ void twist_item(const typename G::W* cur, typename G::W* nxt, int v,
+                                           typename G::W (&z)[VW], const ShiftK& k)
+{
+    typename G::W nw[VW];
+    twist_vec<G, M, VW, K0, K1>(cur, nxt, v, nw, k);
+#pragma unroll
+    for (int u = 0; u < VW; ++u) z[u] = G::temper(nw[u], k);
 }
 
 // One phase of the block twist: rows [K0, K1).  When the whole phase is
@@ -83,9 +91,12 @@ __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G
             for (int i = 0; i < ITEMS; ++i) {
                 const int v = V0 + tid + i * T;
                 if (((i + 1) * T <= V1 - V0) || v < V1) {
-                    W z[VW];
-                    twist_item<G, M, VW, K0, K1>(cur, nxt, v, z, em.a.k);
+                    W nw[VW], z[VW];
+                    twist_vec<G, M, VW, K0, K1>(cur, nxt, v, nw, em.a.k);
                     const int f0 = v * VW;
+                    if (f0 >= hi) continue;   // past the call's output: the state only
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) z[u] = G::temper(nw[u], em.a.k);
                     if (f0 + VW <= hi) {
                         if (P::nseg == 2 && f0 >= plan.b1)
                             store_typed<(P::nseg == 2 ? P::DT1 : P::DT0), W, VW>(plan.base1, f0, z);
@@ -208,6 +219,7 @@ __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(
         const int p = UNITS ? *posp : a.pos;
         int final_pos = p;
         Plan plan;
+        bool have_plan = false;   // typed plans: the next block's is the current one advanced by B
         if (p < B && total > 0) {
             // rest of the current block: block word f is call word f - p
             const int hi = min(B, p + total);
@@ -248,11 +260,18 @@ __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(
             }
             e = hi - p;
             final_pos = hi;
+            have_plan = true;
         }
         while (e < total) {
             const int hi = min(B, total - e);   // block words [0, hi) are emitted
             const bool check = hi < B;
-            plan.template make<P, W, VW>(a, em, e);
+            if constexpr (!P::generic) {
+                if (have_plan) plan.template advance<P, W, VW>(B);
+                else plan.template make<P, W, VW>(a, em, e);
+                have_plan = true;
+            } else {
+                plan.template make<P, W, VW>(a, em, e);
+            }
             twist_phase<G, M, VW, T, P, 0, NM>(cur, nxt, plan, em, hi, e, check);
             __syncthreads();
             twist_phase<G, M, VW, T, P, NM, (2 * NM < N ? 2 * NM : N)>(cur, nxt, plan, em, hi, e, check);
