@@ -12,60 +12,64 @@
 // old block, later rows read the new word x'_{k-(n-m)} written (n-m) rows
 // earlier.  Cutting the block every n-m rows therefore gives phases whose rows
 // are independent (MT19937-32: 227/227/170 rows, MT19937-64: 156/156 rows).
-// Within a phase, row k also reads the old x_{k+1} that row k+1 overwrites, so
-// each phase loads all operands, synchronises, then writes.
+// The two copies of X-hat (old block read, new block written) let a phase
+// load and store without a barrier in between.
+//
+// Any cut works as long as no item (one vector of M / VW lanes of a row)
+// shares a pass with the item (n-m) rows before it; twist_block picks the cut
+// (MT19937-32 with 16 lanes and 512 threads: 2496 items in five passes of one
+// item per thread instead of three phases of up to two items each).
 #include "bulk.cuh"
 #include "gen_mt.cuh"
 
 namespace vmt {
 namespace dev {
 
-// One item of a twist phase: vector v of the new block from the old block
-// `cur` and the rows of `nxt` finished by earlier phases.
-// the new words of vector v (written to nxt and returned in nw)
-template <class G, int M, int VW, int K0, int K1>
+// One item of a pass over vectors [V0, V1) of the block: vector v of the new
+// block from the old block `cur` and the rows of `nxt` finished by earlier
+// passes; the new words are written to nxt and returned in nw.
+template <class G, int M, int VW, int V0, int V1>
 __device__ __forceinline__ void twist_vec(const typename G::W* cur, typename G::W* nxt, int v,
                                           typename G::W (&nw)[VW], const ShiftK& k)
 {
     using W = typename G::W;
     constexpr int N = G::N, MM = G::MM, NM = N - MM;
-    constexpr int RV = M / VW, NV = N * RV;
+    constexpr int RV = M / VW, NV = N * RV, DV = NM * RV;
     W xa[VW], xb[VW], xc[VW];
     ldv<W, VW>(cur + v * VW, xa);
-    if (K1 < N || v + RV < NV) ldv<W, VW>(cur + (v + RV) * VW, xb);   // old x_{k+1}
-    else ldv<W, VW>(nxt + (v + RV - NV) * VW, xb);                    // new x_0 for the last row
-    if (K0 == 0) ldv<W, VW>(cur + (v + MM * RV) * VW, xc);          // old x_{k+m}
-    else ldv<W, VW>(nxt + (v - NM * RV) * VW, xc);                  // new x_{k-(n-m)}
+    if (V1 <= NV - RV || v + RV < NV) ldv<W, VW>(cur + (v + RV) * VW, xb);   // old x_{k+1}
+    else ldv<W, VW>(nxt + (v + RV - NV) * VW, xb);                          // new x_0 for the last row
+    if (V1 <= DV || (V0 < DV && v < DV)) ldv<W, VW>(cur + (v + MM * RV) * VW, xc);   // old x_{k+m}
+    else ldv<W, VW>(nxt + (v - DV) * VW, xc);                                      // new x_{k-(n-m)}
 #pragma unroll
     for (int u = 0; u < VW; ++u) nw[u] = G::twist(xa[u], xb[u], xc[u], k);
     stv<W, VW>(nxt + v * VW, nw);
 }
 
-template <class G, int M, int VW, int K0, int K1>
+template <class G, int M, int VW, int V0, int V1>
 __device__ __forceinline__ void twist_item(const typename G::W* cur, typename G::W* nxt, int v,
                                            typename G::W (&z)[VW], const ShiftK& k)
 {
     typename G::W nw[VW];
-    twist_vec<G, M, VW, K0, K1>(cur, nxt, v, nw, k);
+    twist_vec<G, M, VW, V0, V1>(cur, nxt, v, nw, k);
 #pragma unroll
     for (int u = 0; u < VW; ++u) z[u] = G::temper(nw[u], k);
 }
 
-// One phase of the block twist: rows [K0, K1).  When the whole phase is
-// emitted into one statically typed segment (the common case) the items run
-// without any per-vector check; otherwise every vector is routed by emit_p.
-template <class G, int M, int VW, int T, class P, int K0, int K1>
-__device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G::W* nxt,
-                                            const typename PlanOf<P>::type& plan, const Emitter& em, int hi,
-                                            long long e, bool check)
+// One pass of the block twist: vectors [V0, V1), thread tid taking V0 + tid,
+// V0 + tid + T, ...  When the whole pass is emitted into one statically typed
+// segment (the common case) the items run without any per-vector check;
+// otherwise every vector is routed by emit_p.
+template <class G, int M, int VW, int T, class P, int V0, int V1>
+__device__ __forceinline__ void twist_pass(const typename G::W* cur, typename G::W* nxt,
+                                           const typename PlanOf<P>::type& plan, const Emitter& em, int hi,
+                                           long long e, bool check)
 {
     using W = typename G::W;
-    constexpr int RV = M / VW;
-    constexpr int V0 = K0 * RV, V1 = K1 * RV;
     constexpr int ITEMS = (V1 - V0 + T - 1) / T;
     const int tid = threadIdx.x;
     if constexpr (!P::generic) {
-        const bool inside = !check || V1 * VW <= hi;   // every vector of the phase is emitted
+        const bool inside = !check || V1 * VW <= hi;   // every vector of the pass is emitted
         if (inside && plan.ok && (P::nseg == 1 || plan.b1 >= V1 * VW || plan.b1 <= V0 * VW)) {
             const bool second = P::nseg == 2 && plan.b1 <= V0 * VW;
             const long long base = second ? plan.base1 : plan.base0;
@@ -74,7 +78,7 @@ __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G
                 const int v = V0 + tid + i * T;
                 if (((i + 1) * T <= V1 - V0) || v < V1) {
                     W z[VW];
-                    twist_item<G, M, VW, K0, K1>(cur, nxt, v, z, em.a.k);
+                    twist_item<G, M, VW, V0, V1>(cur, nxt, v, z, em.a.k);
                     if (P::nseg == 2 && second) store_typed<(P::nseg == 2 ? P::DT1 : P::DT0), W, VW>(base, v * VW, z);
                     else store_typed<P::DT0, W, VW>(base, v * VW, z);
                 }
@@ -82,7 +86,7 @@ __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G
             return;
         }
         if (plan.ok) {
-            // a phase that holds the end of the call's output or the segment
+            // a pass that holds the end of the call's output or the segment
             // boundary: a whole vector inside [0, hi) takes the typed store of
             // its segment (the boundary falls between vectors), the vector
             // that straddles hi the word path, vectors at or beyond hi only
@@ -92,7 +96,7 @@ __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G
                 const int v = V0 + tid + i * T;
                 if (((i + 1) * T <= V1 - V0) || v < V1) {
                     W nw[VW], z[VW];
-                    twist_vec<G, M, VW, K0, K1>(cur, nxt, v, nw, em.a.k);
+                    twist_vec<G, M, VW, V0, V1>(cur, nxt, v, nw, em.a.k);
                     const int f0 = v * VW;
                     if (f0 >= hi) continue;   // past the call's output: the state only
 #pragma unroll
@@ -115,13 +119,54 @@ __device__ __forceinline__ void twist_phase(const typename G::W* cur, typename G
         const int v = V0 + tid + i * T;
         const bool act = ((i + 1) * T <= V1 - V0) || v < V1;   // static for all but the last item
         W z[VW];
-        if (act) twist_item<G, M, VW, K0, K1>(cur, nxt, v, z, em.a.k);
+        if (act) twist_item<G, M, VW, V0, V1>(cur, nxt, v, z, em.a.k);
         else {
 #pragma unroll
             for (int u = 0; u < VW; ++u) z[u] = W(0);
         }
         emit_p<P, W, VW>(plan, em, v * VW, z, 0, hi, e, act, check);
     }
+}
+
+// Passes of the block twist.  A pass may hold up to (n-m) M / VW vectors (no
+// vector of it depends on another of it); with T threads a pass of s vectors
+// costs ceil(s / T) item slots per thread and one barrier.  Two cuts:
+//   * phase form: the row ranges [0, n-m), [n-m, 2(n-m)), [2(n-m), n);
+//   * wave form: passes of the largest multiple of T that fits, so that no
+//     thread idles at a barrier while others finish an extra item.
+// The cheaper one is taken, a barrier counted as 0.4 item slots (measured:
+// MT19937-32, 16 lanes, 512 threads, 5 slots + 5 barriers beat 6 + 3, and
+// MT19937-64, 8 lanes, 256 threads, 6 slots + 2 barriers beat 5 + 5).
+__host__ __device__ constexpr int pass_slots(int nv, int step, int t)
+{
+    int s = 0;
+    for (int v = 0; v < nv; v += step) s += ((nv - v < step ? nv - v : step) + t - 1) / t;
+    return s;
+}
+
+__host__ __device__ constexpr int pass_step(int nv, int dv, int t)
+{
+    if (t > dv) return dv;
+    const int wave = t * (dv / t);
+    const int cost_wave = 10 * pass_slots(nv, wave, t) + 4 * ((nv + wave - 1) / wave);
+    const int cost_phase = 10 * pass_slots(nv, dv, t) + 4 * ((nv + dv - 1) / dv);
+    return cost_wave < cost_phase ? wave : dv;
+}
+
+// The passes from vector V0 on, each followed by a barrier.
+template <class G, int M, int VW, int T, class P, int V0>
+__device__ __forceinline__ void twist_block(const typename G::W* cur, typename G::W* nxt,
+                                            const typename PlanOf<P>::type& plan, const Emitter& em, int hi,
+                                            long long e, bool check)
+{
+    constexpr int N = G::N, NM = N - G::MM;
+    constexpr int RV = M / VW, NV = N * RV, DV = NM * RV;
+    constexpr int STEP = pass_step(NV, DV, T);
+    static_assert(STEP >= 1 && STEP <= DV, "a pass holds no dependent vectors");
+    constexpr int V1 = V0 + STEP < NV ? V0 + STEP : NV;
+    twist_pass<G, M, VW, T, P, V0, V1>(cur, nxt, plan, em, hi, e, check);
+    __syncthreads();
+    if constexpr (V1 < NV) twist_block<G, M, VW, T, P, V1>(cur, nxt, plan, em, hi, e, check);
 }
 
 // set by a kernel whose bounded wait on a bulk copy gave up
@@ -146,13 +191,13 @@ template <class G, int M, int VW, int T, class P, bool UNITS>
 __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(GenArgs a)
 {
     using W = typename G::W;
-    constexpr int N = G::N, MM = G::MM, NM = N - MM;
+    constexpr int N = G::N;
     constexpr int B = N * M;        // words per block
     constexpr uint32_t BYTES = static_cast<uint32_t>(B * sizeof(W));
-    static_assert(N <= 3 * NM, "at most three phases");
+    static_assert(N <= 3 * (N - G::MM), "at most three phases in the phase form");
     static_assert(BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
     // two copies of X-hat: the old block is only read while the new one is
-    // written, so a phase needs no barrier between its loads and its stores.
+    // written, so a pass needs no barrier between its loads and its stores.
     // A generator's state arrives and leaves with one bulk copy each; the
     // next generator's state is fetched into the idle copy while the finished
     // one is written back.
@@ -219,7 +264,6 @@ __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(
         const int p = UNITS ? *posp : a.pos;
         int final_pos = p;
         Plan plan;
-        bool have_plan = false;   // typed plans: the next block's is the current one advanced by B
         if (p < B && total > 0) {
             // rest of the current block: block word f is call word f - p
             const int hi = min(B, p + total);
@@ -260,26 +304,12 @@ __global__ void __launch_bounds__(T, (mt_ctas_per_sm<G, M, T>())) gen_mt_kernel(
             }
             e = hi - p;
             final_pos = hi;
-            have_plan = true;
         }
         while (e < total) {
             const int hi = min(B, total - e);   // block words [0, hi) are emitted
             const bool check = hi < B;
-            if constexpr (!P::generic) {
-                if (have_plan) plan.template advance<P, W, VW>(B);
-                else plan.template make<P, W, VW>(a, em, e);
-                have_plan = true;
-            } else {
-                plan.template make<P, W, VW>(a, em, e);
-            }
-            twist_phase<G, M, VW, T, P, 0, NM>(cur, nxt, plan, em, hi, e, check);
-            __syncthreads();
-            twist_phase<G, M, VW, T, P, NM, (2 * NM < N ? 2 * NM : N)>(cur, nxt, plan, em, hi, e, check);
-            __syncthreads();
-            if constexpr (2 * NM < N) {
-                twist_phase<G, M, VW, T, P, (2 * NM < N ? 2 * NM : N), N>(cur, nxt, plan, em, hi, e, check);
-                __syncthreads();
-            }
+            plan.template make<P, W, VW>(a, em, e);
+            twist_block<G, M, VW, T, P, 0>(cur, nxt, plan, em, hi, e, check);
             W* t = cur;
             cur = nxt;
             nxt = t;

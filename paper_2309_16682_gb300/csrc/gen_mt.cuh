@@ -260,56 +260,24 @@ struct TypedPlan {
     long long base0, base1;
     int b1;
     bool ok;
-    long long b1_full;   // the boundary before clamping
-    bool bases_ok;       // both bases aligned to a vector (invariant under advance)
-    bool b1_aligned;     // the boundary on a vector (invariant under advance)
-
-    // the plan of the next block: block word f of the next block is call
-    // word f + delta + dB (both bases move by dB words, the boundary by -dB);
-    // dB is a whole number of vectors, so the alignments do not change
-    template <class P, typename W, int VW>
-    __device__ __forceinline__ void advance(int dB)
-    {
-        base0 += static_cast<long long>(dB) * bytes_per_word<W>(P::DT0);
-        if constexpr (P::nseg == 2) {
-            base1 += static_cast<long long>(dB) * bytes_per_word<W>(P::DT1);
-            b1_full -= dB;
-            long long b = b1_full;
-            if (b < -1) b = -1;
-            if (b > (1LL << 30)) b = 1LL << 30;
-            b1 = static_cast<int>(b);
-            ok = bases_ok && (b1_aligned || b <= 0 || b >= (1LL << 30));
-        }
-    }
 
     template <class P, typename W, int VW>
     __device__ __forceinline__ void make(const GenArgs& a, const Emitter& em, long long delta)
     {
         const int bpw0 = bytes_per_word<W>(P::DT0);
-        const int esz0 = (P::DT0 == VMT_U32 || P::DT0 == VMT_F32) ? 4 : 8;
-        (void)esz0;
         base0 = reinterpret_cast<long long>(em.elem0(0)) + (delta - a.seg[0].wbeg) * bpw0;
         ok = (base0 % (VW * bpw0)) == 0;
         b1 = 0x7FFFFFFF;
         base1 = 0;
         if constexpr (P::nseg == 2) {
             const int bpw1 = bytes_per_word<W>(P::DT1);
-            const int esz1 = (P::DT1 == VMT_U32 || P::DT1 == VMT_F32) ? 4 : 8;
-            (void)esz1;
             base1 = reinterpret_cast<long long>(em.elem0(1)) + (delta - a.seg[1].wbeg) * bpw1;
             ok = ok && (base1 % (VW * bpw1)) == 0;
             long long b = a.seg[1].wbeg - delta;
-            b1_full = b;
-            b1_aligned = (b % VW) == 0;
-            bases_ok = ok;
             if (b < -1) b = -1;
             if (b > (1LL << 30)) b = 1LL << 30;
             b1 = static_cast<int>(b);
-            if (b > 0 && b < (1LL << 30) && !b1_aligned) ok = false;
-        } else {
-            bases_ok = ok;
-            b1_full = 0;
-            b1_aligned = true;
+            if (b > 0 && b < (1LL << 30) && (b % VW) != 0) ok = false;
         }
     }
 };
