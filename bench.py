@@ -385,7 +385,10 @@ def run_served(vmt, requests: int, rate: float, plain_requests: int, client: str
                max(1, stats["express_completed"] - stats0["express_completed"]),
                "express_mean_running_ms": 1e3 * (stats["express_running_s"] - stats0["express_running_s"]) /
                max(1, stats["express_completed"] - stats0["express_completed"]),
+               "express_gpu_span_ms_per_batch": 1e3 * (stats["express_batch_gpu_s"] - stats0["express_batch_gpu_s"]) /
+               max(1, stats["express_batches"] - stats0["express_batches"]),
                "mean_submit_lag_ms": 1e3 * float(np.mean(lag_all)) if lag_all else None,
+               "hw_work_queues": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
                "client": client}
     # plain form on the first plain_requests requests of the same trace
     pr = reqs[:plain_requests]

@@ -176,11 +176,17 @@ void vmt_batch_destroy(vmt_batch* b);
  * as they arrive, at most max_batch (1..4096) per batch: batched seeding and
  * jump-ahead on one stream, a persistent ragged generation (longest first) on
  * another, so a new batch's initialisation overlaps the previous batch's
- * generation.  Requests of at most 16,384 outputs may also go ahead of the
- * queue, in batches of their own on an extra slot with high-priority streams;
- * their outputs count against an express budget of output_budget_bytes / 16
- * instead of the output budget, and they pass a waiting request only where it
- * would still fit the state budget afterwards.
+ * generation.  Requests of at most 16,384 outputs whose bytes fit the express
+ * budget (output_budget_bytes / 16) run only in express batches: one slot per
+ * variant with the highest-priority streams, ahead of the queue; their
+ * outputs count against the express budget instead of the output budget, and
+ * they pass a waiting request only where it would still fit the state budget
+ * afterwards.
+ * Latency: the server runs up to 29 streams at once.  CUDA maps streams onto
+ * CUDA_DEVICE_MAX_CONNECTIONS hardware work queues (8 unless set before the
+ * process creates its CUDA context), and work of streams that share a queue
+ * is serialised: with 8, small requests wait behind long requests' jump
+ * chains.  Set it to 32 (the Python package does so on import when unset).
  *   vmt_server_submit   never blocks; *id names the request
  *   vmt_server_poll     status VMT_SERVER_QUEUED / RUNNING / DONE or a negative
  *                       VMT_E* code (that request failed; the server goes on);
@@ -229,6 +235,8 @@ typedef struct {
      * of the time running (admission to completion), regular and express */
     int64_t express_batches, express_completed;
     double queued_s, running_s, express_queued_s, express_running_s;
+    /* the express batches' share of init_gpu_s and batch_gpu_s */
+    double express_init_gpu_s, express_batch_gpu_s;
 } vmt_server_counters;
 
 int vmt_server_create(vmt_server** s, const vmt_server_config* cfg);

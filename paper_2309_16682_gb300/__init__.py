@@ -18,6 +18,15 @@ import threading
 
 import numpy as np
 
+# The server keeps many streams busy at once (per batch slot one stream per
+# variant's initialisation and one for generation).  CUDA multiplexes streams
+# onto a fixed number of hardware work queues, 8 by default, and kernels of
+# unrelated streams that share a queue wait for each other: a small request's
+# launches then queue behind a long request's jump chain.  The count is read
+# when the process creates its CUDA context, so it is set here, on import,
+# unless the caller has chosen one (32 is CUDA's maximum).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libvmt.so")
 CACHE_DIR = os.path.join(HERE, "_cache")
@@ -303,7 +312,8 @@ class _Counters(ctypes.Structure):
                                              "peak_state_bytes", "peak_output_bytes")] + \
         [(n, ctypes.c_double) for n in ("host_launch_s", "init_gpu_s", "batch_gpu_s")] + [("cancelled", ctypes.c_int64)] + \
         [(n, ctypes.c_int64) for n in ("express_batches", "express_completed")] + \
-        [(n, ctypes.c_double) for n in ("queued_s", "running_s", "express_queued_s", "express_running_s")]
+        [(n, ctypes.c_double) for n in ("queued_s", "running_s", "express_queued_s", "express_running_s",
+                                        "express_init_gpu_s", "express_batch_gpu_s")]
 
 
 class Server:

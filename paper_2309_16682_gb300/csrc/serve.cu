@@ -16,9 +16,10 @@
 // function that stamps the requests' completion times.
 //
 // Requests of at most kExpressOutputs outputs may also go ahead of the queue
-// in a batch of their own on a fifth slot, whose generation stream has the
-// high priority of the init streams: their latency is then a few short
-// launches, not the queue plus a batch of long requests.  Their outputs count
+// in batches of their own on express slots, one per variant, whose streams
+// have the highest priority: their latency is then a few short launches, not
+// the queue plus a batch of long requests, and a small MT19937 request never
+// waits for an SFMT19937 jump chain.  Their outputs count
 // against an express budget (a sixteenth of the output budget), so they never
 // take output memory that a waiting request needs; they pass others only where
 // the first request they pass still fits the state budget afterwards.
@@ -66,10 +67,13 @@ int64_t n_chunks(int variant, int lanes, int64_t w)
     return std::min<int64_t>((w + C - 1) / C, vmt::kChunkRows + 1);
 }
 
-constexpr int kSlots = 5;          // batches that may be in flight at once
-constexpr int kExpress = kSlots - 1;   // the slot kept for small requests only
+constexpr int kRegular = 4;                 // slots for batches of any request
+constexpr int kSlots = kRegular + 3;        // + one express slot per variant (small requests only)
+inline bool is_express(int slot) { return slot >= kRegular; }
+inline int express_slot(int variant) { return kRegular + variant; }
 constexpr int64_t kExpressOutputs = 16384;   // "small": at most this many outputs
-constexpr size_t kExpressScan = 4096;        // queue entries an express batch looks at
+constexpr size_t kExpressScan = 4096;        // queue entries an admission pass looks at
+constexpr bool kSmallWaitsForExpress = true; // small requests run only in express batches
 constexpr int kMaxGroups = 16;     // kernels per batch
 constexpr int kMaxUnits = 65536;   // units (requests or chunks of requests) per batch
 
@@ -135,6 +139,7 @@ struct vmt_server {
     int64_t cancelled = 0;
     int64_t express_batches = 0, express_completed = 0;
     double queued_s = 0, running_s = 0, express_queued_s = 0, express_running_s = 0;
+    double express_init_gpu_s = 0, express_batch_gpu_s = 0;
     std::atomic<int> inject_alloc{0};   // output allocations still to fail (fault injection)
     cudaMemPool_t pool = nullptr;   // states and outputs
     // Memory is freed on a stream of its own, only ever after the kernels that
@@ -355,15 +360,20 @@ void worker_main(vmt_server* s)
         if (!done_slots.empty()) {
             lk.unlock();
             for (const auto& f : to_free) vmt::free_state_async(f.first, f.second);
-            float t_init = 0, t_all = 0, ms = 0;
+            float t_init = 0, t_all = 0, x_init = 0, x_all = 0, ms = 0;
             for (int i : done_slots) {
-                if (cudaEventElapsedTime(&ms, s->slots[i].ev[0], s->slots[i].ev[1]) == cudaSuccess) t_init += ms;
-                if (cudaEventElapsedTime(&ms, s->slots[i].ev[0], s->slots[i].ev[2]) == cudaSuccess) t_all += ms;
+                const bool x = is_express(i);
+                if (cudaEventElapsedTime(&ms, s->slots[i].ev[0], s->slots[i].ev[1]) == cudaSuccess)
+                    (x ? x_init : t_init) += ms;
+                if (cudaEventElapsedTime(&ms, s->slots[i].ev[0], s->slots[i].ev[2]) == cudaSuccess)
+                    (x ? x_all : t_all) += ms;
             }
             cudaGetLastError();
             lk.lock();
-            s->init_gpu_s += 1e-3 * t_init;
-            s->batch_gpu_s += 1e-3 * t_all;
+            s->init_gpu_s += 1e-3 * (t_init + x_init);
+            s->batch_gpu_s += 1e-3 * (t_all + x_all);
+            s->express_init_gpu_s += 1e-3 * x_init;
+            s->express_batch_gpu_s += 1e-3 * x_all;
             for (int i : done_slots) s->slots[i].busy = false;
         }
         if (s->stop && s->queue.empty() && s->inflight.empty()) break;
@@ -390,12 +400,14 @@ void worker_main(vmt_server* s)
             ids.push_back(id);
         };
         int slot = -1;
-        if (!s->slots[kExpress].busy) {
-            // express batch: small requests go ahead of the queue on a slot of
-            // their own, so that they never wait behind long ones.  Their
-            // outputs count against an express budget of their own; the first
-            // queued request they pass keeps its claim on the state budget: a
-            // small request goes ahead only if that one would still fit after it.
+        for (int v = VMT_MT19937_32; v <= VMT_SFMT19937 && slot < 0; ++v) {
+            if (s->slots[express_slot(v)].busy) continue;
+            // express batch of variant v: its small requests go ahead of the
+            // queue on a slot of their own, so that they never wait behind
+            // long ones nor behind another variant's jumps.  Their outputs
+            // count against an express budget of their own; the first queued
+            // request they pass keeps its claim on the state budget: a small
+            // request goes ahead only if that one would still fit after it.
             const int64_t express_budget = s->cfg.output_budget_bytes / 16;
             int64_t claim_state = 0;
             bool claimed = false;
@@ -412,37 +424,48 @@ void worker_main(vmt_server* s)
                     ++k;
                     continue;
                 }
+                if (q.r.variant != v) {
+                    ++k;
+                    continue;
+                }
                 if (s->used_state + add_state + q.state_bytes + claim_state > s->cfg.state_budget_bytes ||
                     s->used_out_express + q.bytes > express_budget || !fits_batch(q))
                     break;
                 admit(q, id, true);
                 s->queue.erase(s->queue.begin() + static_cast<std::ptrdiff_t>(k));
             }
-            if (!rq.empty()) slot = kExpress;
+            if (!rq.empty()) slot = express_slot(v);
         }
         if (slot < 0)
-            for (int i = 0; i < kExpress; ++i)
+            for (int i = 0; i < kRegular; ++i)
                 if (!s->slots[i].busy) {
                     slot = i;
                     break;
                 }
-        // admission: FIFO, as long as both budgets hold
-        while (slot >= 0 && slot != kExpress && !s->queue.empty() && static_cast<int>(rq.size()) < s->cfg.max_batch) {
-            const uint64_t id = s->queue.front();
+        // admission: FIFO, as long as both budgets hold; small requests that
+        // the express budget can hold are left to the express slots (a
+        // regular batch would make them wait for its longest request)
+        for (size_t k = 0; slot >= 0 && !is_express(slot) && k < s->queue.size() && k < kExpressScan &&
+                           static_cast<int>(rq.size()) < s->cfg.max_batch;) {
+            const uint64_t id = s->queue[k];
             Req& q = s->reqs[id];
             if (q.state_bytes > s->cfg.state_budget_bytes || q.bytes > s->cfg.output_budget_bytes) {
                 q.status = VMT_ENOMEM;   // can never be admitted
                 ++s->failed;
                 s->done_q.push_back(id);
-                s->queue.pop_front();
+                s->queue.erase(s->queue.begin() + static_cast<std::ptrdiff_t>(k));
                 s->cv_done.notify_all();
+                continue;
+            }
+            if (kSmallWaitsForExpress && q.r.n <= kExpressOutputs && q.bytes <= s->cfg.output_budget_bytes / 16) {
+                ++k;
                 continue;
             }
             if (s->used_state + add_state + q.state_bytes > s->cfg.state_budget_bytes ||
                 s->used_out + q.bytes > s->cfg.output_budget_bytes || !fits_batch(q))
                 break;
             admit(q, id, false);
-            s->queue.pop_front();
+            s->queue.erase(s->queue.begin() + static_cast<std::ptrdiff_t>(k));
         }
         if (rq.empty()) {
             // nothing to launch: sleep until a submit, a release or a finished
@@ -460,7 +483,7 @@ void worker_main(vmt_server* s)
         b->cb = HostDone{s, b};
         s->slots[slot].busy = true;
         ++s->batches;
-        if (slot == kExpress) ++s->express_batches;
+        if (is_express(slot)) ++s->express_batches;
         lk.unlock();
         const double t0 = now_s();
         const int rc = launch_batch(s, b, rq);
@@ -526,7 +549,14 @@ int vmt_server_create(vmt_server** out, const vmt_server_config* cfg)
     bool ok = cudaMemPoolCreate(&s->pool, &props) == cudaSuccess;
     if (ok) {
         uint64_t keep = static_cast<uint64_t>(cfg->state_budget_bytes) + static_cast<uint64_t>(cfg->output_budget_bytes);
+        // A block freed on one stream is never handed to an allocation on
+        // another by making the second stream wait for the first: the init
+        // streams free their scratch at the end of long jump chains, and an
+        // express batch must not queue behind a regular batch's chain for
+        // its memory.  Blocks whose frees have completed are still reused.
+        int no_wait = 0;
         ok = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess &&
+             cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no_wait) == cudaSuccess &&
              cudaStreamCreateWithFlags(&s->s_free, cudaStreamNonBlocking) == cudaSuccess;
     }
     // three priorities: the express slot's work above the regular slots'
@@ -542,7 +572,7 @@ int vmt_server_create(vmt_server** out, const vmt_server_config* cfg)
         // blocks still waiting for an SM (every generation unit has its own
         // CTA, so an SM frees up whenever one finishes); the express slot's
         // initialisation and generation go ahead of both
-        ok = cudaStreamCreateWithPriority(&sl.s_gen, cudaStreamNonBlocking, i == kExpress ? prio_hi : prio_lo) ==
+        ok = cudaStreamCreateWithPriority(&sl.s_gen, cudaStreamNonBlocking, is_express(i) ? prio_hi : prio_lo) ==
                  cudaSuccess &&
              cudaHostAlloc(reinterpret_cast<void**>(&sl.h_units), nu * sizeof(vmt::UnitDesc), 0) == cudaSuccess &&
              cudaMalloc(reinterpret_cast<void**>(&sl.d_units), nu * sizeof(vmt::UnitDesc)) == cudaSuccess &&
@@ -555,7 +585,7 @@ int vmt_server_create(vmt_server** out, const vmt_server_config* cfg)
             ok = cudaEventCreate(&sl.ev[e]) == cudaSuccess &&
                  cudaEventCreateWithFlags(&sl.ev_init[e], cudaEventDisableTiming) == cudaSuccess &&
                  cudaStreamCreateWithPriority(&sl.s_init[e], cudaStreamNonBlocking,
-                                              i == kExpress ? prio_hi : prio_init) == cudaSuccess;
+                                              is_express(i) ? prio_hi : prio_init) == cudaSuccess;
     }
     if (ok && cfg->reserve) {
         // map the budgets now: one allocation of their sum, freed back to the pool
@@ -807,6 +837,8 @@ int vmt_server_stats(vmt_server* s, vmt_server_counters* out)
     out->running_s = s->running_s;
     out->express_queued_s = s->express_queued_s;
     out->express_running_s = s->express_running_s;
+    out->express_init_gpu_s = s->express_init_gpu_s;
+    out->express_batch_gpu_s = s->express_batch_gpu_s;
     return VMT_OK;
 }
 

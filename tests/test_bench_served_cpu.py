@@ -71,7 +71,8 @@ class FakeServer:
     def stats(self):
         return {"batches": self.batches, "peak_output_bytes": 0, "host_launch_s": 0.0,
                 "init_gpu_s": 0.0, "batch_gpu_s": 0.0, "express_batches": 0, "express_completed": 0,
-                "queued_s": 0.0, "running_s": 0.0, "express_queued_s": 0.0, "express_running_s": 0.0}
+                "queued_s": 0.0, "running_s": 0.0, "express_queued_s": 0.0, "express_running_s": 0.0,
+                "express_init_gpu_s": 0.0, "express_batch_gpu_s": 0.0}
 
     def close(self):
         pass

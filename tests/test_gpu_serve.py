@@ -342,3 +342,28 @@ def test_small_request_goes_ahead_of_long_ones(vmt):
     for rid in order:
         srv.release(rid)
     srv.close()
+
+
+def test_small_requests_run_only_in_express_batches_one_variant_each(vmt):
+    # Long requests keep the regular slots busy; small requests of all three
+    # variants, submitted together, all run in express batches (never in a
+    # regular batch), an express batch holds one variant only (so at least
+    # three of them), and every output equals the request run alone.
+    srv = vmt.Server(state_budget=2 << 30, output_budget=32 << 30, max_batch=64)
+    st0 = srv.stats()
+    n = (1 << 30) - 1
+    longs = [srv.submit("mt32", 16, "u32", 200 + i, 0, n) for i in range(5)]
+    cases = [("mt32", 8, "u32", 11, 5, 3000), ("mt64", 4, "u64", 12, 6, 2000), ("sfmt", 16, "f32", 13, 7, 16384),
+             ("mt32", 16, "f32", 14, 0, 100), ("sfmt", 4, "u32", 15, 2**40 + 9, 4096), ("mt64", 16, "f64", 16, 3, 16384)]
+    small = srv.submit_many(vmt.Server.requests(cases), 0, len(cases)).tolist()
+    for rid in longs + small:
+        srv.wait(rid, timeout_ms=60_000)
+        assert srv.poll(rid)[0] == vmt.SERVER_DONE
+    st1 = srv.stats()
+    assert st1["express_completed"] - st0["express_completed"] == len(small)
+    assert st1["express_batches"] - st0["express_batches"] >= 3
+    for rid, c in zip(small, cases):
+        assert np.array_equal(srv.copy(rid, c[2]), _alone(vmt, *c)), c
+    for rid in longs + small:
+        srv.release(rid)
+    srv.close()
