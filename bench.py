@@ -725,7 +725,7 @@ def run_gb300(args, world, rank, local):
             "roofline": roof,
             "words_per_s": sum(n * count for n, _ in segs) * args.steps * world / (total_ms / 1e3),
             "step_ms": {"best": float(np.min(per_step)), "median": float(np.median(per_step)),
-                        "mean": float(np.mean(per_step))},
+                        "mean": float(np.mean(per_step)), "each": [round(float(t), 4) for t in per_step]},
             "gpu_launches": args.steps,
             "tuning": {"kernel": tune_kernel, "autotune": tuned},
             "e2e": e2e,
