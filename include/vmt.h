@@ -333,10 +333,14 @@ int vmt_device_status(int reset);
  * of eq. (stepnomod) is spread over a CTA is a GPU-specific choice).  Each
  * (variant, lanes) pair of MT19937-32/64 has a small list of compiled kernel
  * configurations, described by vmt_tune_kernels as four ints each:
- *   form           0: phase form -- one CTA per generator, every phase of
- *                     n-m rows spread over all threads, a barrier between
- *                     phases; 1: chain form -- a thread owns the rows j,
- *                     j+(n-m), j+2(n-m) of one column (one barrier per block)
+ *   form           0: phase form -- one CTA per generator, two copies of
+ *                     X-hat in shared memory, each pass of at most n-m rows
+ *                     spread over all threads, a barrier between passes;
+ *                     1: chain form -- a thread owns the rows j, j+(n-m),
+ *                     j+2(n-m) of one column (one barrier per block);
+ *                     2: in-place phase form -- one copy of X-hat, so more
+ *                     CTAs share an SM (default for 16-lane MT19937-32
+ *                     and 8-lane MT19937-64)
  *   lanes_per_cta  lanes of the generator one CTA owns (chain form: M/lanes
  *                     CTAs share a generator; unit launches use one CTA)
  *   threads        CTA size
@@ -351,6 +355,15 @@ int vmt_device_status(int reset);
  *   vmt_tune_kernels   writes min(count, cap) descriptions into desc
  *                      (4 * cap ints) and returns count
  *   vmt_tune_set_kernel / vmt_tune_get_kernel   select / read the index
+ *   vmt_tune_pass_cut  the pass schedule of phase-form (0) or in-place (2)
+ *                      configuration `index`, in units of vectors (VW lane
+ *                      words of one row): out8 = {vectors per block, vectors
+ *                      per pass, vectors per row, vectors in n-m rows,
+ *                      vectors in m rows, threads, in place, early (the next
+ *                      block's first-pass operands are loaded during the last
+ *                      pass)}; VMT_EINVAL for the
+ *                      chain form, SFMT19937 or an index out of range.  Needs
+ *                      no GPU; tests check the schedule's hazards with it.
  *   vmt_autotune_grid  times every configuration on `count` generators
  *                      producing the caller's segment list (as
  *                      vmt_generate_multi: counts[i] outputs of dtypes[i] per
@@ -364,6 +377,7 @@ int vmt_device_status(int reset);
 int vmt_tune_set(int variant, int lanes, int threads);
 int vmt_tune_get(int variant, int lanes);
 int vmt_tune_kernels(int variant, int lanes, int* desc, int cap);
+int vmt_tune_pass_cut(int variant, int lanes, int index, int* out8);
 int vmt_tune_set_kernel(int variant, int lanes, int index);
 int vmt_tune_get_kernel(int variant, int lanes);
 int vmt_autotune_grid(int variant, int lanes, int64_t count, int nseg, const int64_t* counts, const int* dtypes,

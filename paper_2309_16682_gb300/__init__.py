@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
             "vmt_autotune": (I, [I, I, I64, I64, I, I, P, P, P]),
             "vmt_autotune_multi": (I, [I, I, I64, I, P, P, I, P, P, P]),
             "vmt_tune_kernels": (I, [I, I, P, I]),
+            "vmt_tune_pass_cut": (I, [I, I, I, P]),
             "vmt_tune_jump_compact": (I, [I, I]),
             "vmt_tgfsr_jump": (I, [P, I64, P, P, I64, I, P]),
             "vmt_server_submit_many": (I, [P, P, I64, P]),
@@ -498,7 +499,7 @@ def tune_get(variant: str, lanes: int) -> int:
     return _check(lib().vmt_tune_get(VARIANTS[variant], int(lanes)))
 
 
-FORMS = {0: "phase", 1: "chain"}
+FORMS = {0: "phase", 1: "chain", 2: "inplace"}
 
 
 def tune_kernels(variant: str, lanes: int) -> list[dict]:
@@ -509,6 +510,15 @@ def tune_kernels(variant: str, lanes: int) -> list[dict]:
     _check(lib().vmt_tune_kernels(VARIANTS[variant], int(lanes), buf, n))
     return [{"form": FORMS[buf[4 * i]], "lanes_per_cta": buf[4 * i + 1], "threads": buf[4 * i + 2],
              "store_bytes": buf[4 * i + 3]} for i in range(n)]
+
+
+def tune_pass_cut(variant: str, lanes: int, index: int) -> dict:
+    """The pass schedule of a phase-form or in-place configuration
+    (vmt_tune_pass_cut), in vectors of one row's VW lane words."""
+    out = (ctypes.c_int * 8)()
+    _check(lib().vmt_tune_pass_cut(VARIANTS[variant], int(lanes), int(index), out))
+    keys = ("vectors", "step", "row_vectors", "n_minus_m_vectors", "m_vectors", "threads", "in_place", "early")
+    return dict(zip(keys, list(out)))
 
 
 def tune_set_kernel(variant: str, lanes: int, index: int) -> None:

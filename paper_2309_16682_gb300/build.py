@@ -21,10 +21,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libvmt.so")
 
-CUDA_SOURCES = ["gen_mt.cu", "gen_mtc32.cu", "gen_mtc64.cu", "gen_sfmt.cu", "gen_sfmt_m1.cu", "gen_sfmt_m2.cu", "gen_sfmt_m4.cu", "gen_sfmt_m8.cu",
+CUDA_SOURCES = ["gen_mt.cu", "gen_mt32.cu", "gen_mt64.cu", "gen_mtc32.cu", "gen_mtc64.cu", "gen_sfmt.cu", "gen_sfmt_m1.cu", "gen_sfmt_m2.cu", "gen_sfmt_m4.cu", "gen_sfmt_m8.cu",
                 "gen_sfmt_m16.cu", "jump.cu", "vmt_capi.cu", "noalloc.cu", "serve.cu", "diag.cu", "scalar.cu", "tgfsr.cu"]
 CXX_SOURCES = ["gf2poly.cpp"]
-HEADERS = ["vmt_device.cuh", "gen_mt.cuh", "gen_mtc.cuh", "vmt_internal.hpp", "gen_args.hpp", "gf2poly.hpp", "bulk.cuh", "gen_sfmt.cuh"]
+HEADERS = ["vmt_device.cuh", "gen_mt.cuh", "gen_mt_kernel.cuh", "gen_mtc.cuh", "vmt_internal.hpp", "gen_args.hpp", "gf2poly.hpp", "bulk.cuh", "gen_sfmt.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -40,17 +40,19 @@ struct UnitDesc {
 };
 
 // Compiled configurations of the MT generation kernels, per (variant, lanes);
-// the first row of a pair is its default.  form: kPhase = one CTA per
+// the first row of a (variant, lanes) group is its default.  form: kPhase = one CTA per
 // generator, all threads on each phase of eq. (stepnomod), a barrier between
 // phases (gen_mt.cu); kChain = a thread owns a chain of rows j, j+(n-m),
-// j+2(n-m), one barrier per block, a CTA owns lpc of the M lanes (gen_mtc*.cu).
+// j+2(n-m), one barrier per block, a CTA owns lpc of the M lanes (gen_mtc*.cu);
+// kInPlace = the phase form on one copy of X-hat (gen_mt.cu).
 // store = bytes per vector store (16 or 8).
-enum { kPhase = 0, kChain = 1 };
+enum { kPhase = 0, kChain = 1, kInPlace = 2 };
 struct KernelCfg {
     int variant, lanes, form, lpc, threads, store;
 };
 constexpr KernelCfg kKernelCfgs[] = {
     // V-MT19937-32
+    {VMT_MT19937_32, 16, kInPlace, 16, 256, 16},
     {VMT_MT19937_32, 16, kPhase, 16, 512, 16},
     {VMT_MT19937_32, 16, kPhase, 16, 1024, 16},
     {VMT_MT19937_32, 16, kChain, 8, 256, 16},
@@ -68,6 +70,8 @@ constexpr KernelCfg kKernelCfgs[] = {
     {VMT_MT19937_64, 16, kPhase, 16, 1024, 16},
     {VMT_MT19937_64, 16, kChain, 4, 160, 16},
     {VMT_MT19937_64, 16, kChain, 8, 320, 16},
+    {VMT_MT19937_64, 16, kInPlace, 16, 256, 16},
+    {VMT_MT19937_64, 8, kInPlace, 8, 256, 16},
     {VMT_MT19937_64, 8, kPhase, 8, 256, 16},
     {VMT_MT19937_64, 8, kPhase, 8, 512, 16},
     {VMT_MT19937_64, 8, kChain, 4, 160, 16},

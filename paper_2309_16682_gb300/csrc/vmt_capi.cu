@@ -1625,6 +1625,15 @@ int vmt_tune_get(int variant, int lanes)
     return c ? c->threads : 0;
 }
 
+int vmt_tune_pass_cut(int variant, int lanes, int index, int* out8)
+{
+    if (!valid_variant(variant) || variant == VMT_SFMT19937 || !valid_lanes(lanes) || !out8)
+        return fail(VMT_EINVAL, "bad argument");
+    if (vmt::pass_cut(variant, lanes, index, out8) != 0)
+        return fail(VMT_EINVAL, "no phase-form configuration with that index");
+    return VMT_OK;
+}
+
 int vmt_tune_kernels(int variant, int lanes, int* desc, int cap)
 {
     if (!valid_variant(variant) || !valid_lanes(lanes) || cap < 0 || (cap > 0 && !desc))

@@ -72,6 +72,9 @@ cudaError_t launch_tgfsr_jump(int n, bool cta, const JumpItem* items, long long 
 
 // ragged: generators of one launch may differ in position or length
 cudaError_t launch_generate(int variant, int lanes, const GenArgs& a, bool ragged, cudaStream_t s);
+// the pass schedule of MT kernel configuration `index` (see vmt_tune_pass_cut);
+// -1 for a chain-form or missing configuration
+int pass_cut(int variant, int lanes, int index, int* out8);
 cudaError_t launch_seed(int variant, long long count, const unsigned long long* seeds, void* base, cudaStream_t s);
 // shared (for launches that share the GPU with long-running kernels, the
 // server's initialisation), whatever the count: 1 every lane-jump on a

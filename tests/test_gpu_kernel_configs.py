@@ -1,7 +1,7 @@
 """Every compiled generation-kernel configuration against the oracle (GPU).
 
 The tuning table selects, per (variant, lanes), one of several compiled
-kernels (phase or chain form, lanes per CTA, CTA size, store width); all must
+kernels (phase, in-place or chain form, lanes per CTA, CTA size, store width); all must
 produce the V-stream exactly.  Each configuration runs the same sequence of
 calls on fresh generators -- lock-step calls across blocks and partial blocks,
 a fused two-segment call (native words then floats), a tiny call, a ragged
@@ -129,12 +129,15 @@ def test_every_kernel_configuration_matches_the_oracle(vmt, oracle_polys, varian
     assert vmt.device_status() == 0
 
 
-@pytest.mark.parametrize("variant,M,form", [(O.MT32, 16, "chain"), (O.MT64, 8, "chain")])
+@pytest.mark.parametrize("variant,M,form", [(O.MT32, 16, "chain"), (O.MT64, 8, "chain"), (O.MT32, 16, "inplace"),
+                                            (O.MT64, 8, "inplace"), (O.MT64, 16, "inplace")])
 def test_more_generators_than_resident_ctas(vmt, oracle_polys, variant, M, form):
-    """Persistent lane-split launches whose CTAs each take many half- or
-    quarter-generators (1500 generators, a few hundred resident CTAs), two
-    calls in a row (the second continues the states the first wrote back),
-    checked on the first, a middle and the last generator."""
+    """1500 generators (for the chain form, half- or quarter-generators): two
+    lock-step calls in a row (the second continues the states the first wrote
+    back), then a ragged call, a persistent launch whose CTAs take generators
+    in turn (in place, every next state is fetched into the copy the previous
+    one was just written from); checked on the first, a middle and the last
+    generator."""
     name = VNAME[variant]
     cands = vmt.tune_kernels(name, M)
     idx = next(i for i, c in enumerate(cands) if c["form"] == form and (form != "chain" or c["lanes_per_cta"] < M))
@@ -142,18 +145,21 @@ def test_more_generators_than_resident_ctas(vmt, oracle_polys, variant, M, form)
     seeds = I.splitmix64(31 + M, 1500)
     native, flt = ("u64", "f64") if variant == O.MT64 else ("u32", "f32")
     segs = [(20000, native), (5000, flt)]
+    ragged = [3000 + 11 * (gi % 97) for gi in range(1500)]   # a persistent unit launch
     try:
         vmt.tune_set_kernel(name, M, idx)
         g = vmt.VGenerator(name, M, seeds)
         a = [_np(t) for t in g.generate_multi(segs)]
         b = [_np(t) for t in g.generate_multi(segs)]
+        c = [_np(t) for t in g.generate_ragged(ragged, native)]
     finally:
         vmt.tune_set_kernel(name, M, prev)
     wpo = O.words_per_output(variant, flt)
     per_call = 20000 + 5000 * wpo
     for gi in (0, 777, 1499):
-        w = O.vstream_words(variant, M, int(seeds[gi]), 2 * per_call, 0)
+        w = O.vstream_words(variant, M, int(seeds[gi]), 2 * per_call + ragged[gi], 0)
         for k, out in enumerate((a, b)):
             base = k * per_call
             assert np.array_equal(out[0][gi], O.convert(variant, w[base:base + 20000], native)), (form, gi, k)
             assert np.array_equal(out[1][gi], O.convert(variant, w[base + 20000:base + per_call], flt)), (form, gi, k)
+        assert np.array_equal(c[gi], O.convert(variant, w[2 * per_call:], native)), (form, gi, "ragged")

@@ -269,14 +269,14 @@ def test_every_cta_size_gives_the_same_stream(vmt, variant, M, threads):
     seeds = I.splitmix64(77, 5)
     native = "u64" if variant == "mt64" else "u32"
     segs = [(3001, native), (9000, "f32"), (12345, native)]
-    prev = vmt.tune_get(variant, M)
+    prev = vmt.tune_get_kernel(variant, M)
     try:
         vmt.tune_set(variant, M, 0)
         ref = [_np(t) for t in vmt.VGenerator(variant, M, seeds).generate_multi(segs)]
         vmt.tune_set(variant, M, threads)
         got = [_np(t) for t in vmt.VGenerator(variant, M, seeds).generate_multi(segs)]
     finally:
-        vmt.tune_set(variant, M, prev)
+        vmt.tune_set_kernel(variant, M, prev)
     for k in range(len(segs)):
         assert np.array_equal(got[k], ref[k])
     assert vmt.device_status() == 0
