@@ -1,7 +1,8 @@
 """Every compiled generation-kernel configuration against the oracle (GPU).
 
 The tuning table selects, per (variant, lanes), one of several compiled
-kernels (phase, in-place or chain form, lanes per CTA, CTA size, store width); all must
+kernels (phase, in-place or chain form, lanes per CTA, CTA size, store
+width); all must
 produce the V-stream exactly.  Each configuration runs the same sequence of
 calls on fresh generators -- lock-step calls across blocks and partial blocks,
 a fused two-segment call (native words then floats), a tiny call, a ragged
