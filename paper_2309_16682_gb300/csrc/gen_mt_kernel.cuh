@@ -21,6 +21,13 @@
 // shares a pass with the item (n-m) rows before it; twist_block picks the cut
 // (MT19937-32 with 16 lanes and 512 threads: 2496 items in five passes of one
 // item per thread instead of three phases of up to two items each).
+//
+// In place (template flag IP): one copy of X-hat, half the shared memory, so
+// that five 256-thread CTAs share an SM.  Of an item's operands only the old
+// x_{k+1} may be overwritten by another thread in the same pass; each thread
+// loads those of its next pass before the barrier that starts it (see
+// preload_next and early_first_preload; tests/test_pass_schedule_cpu.py
+// replays the schedule of every compiled configuration).
 #pragma once
 #include "bulk.cuh"
 #include "gen_mt.cuh"
