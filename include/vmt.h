@@ -339,8 +339,8 @@ int vmt_device_status(int reset);
  *                     1: chain form -- a thread owns the rows j, j+(n-m),
  *                     j+2(n-m) of one column (one barrier per block);
  *                     2: in-place phase form -- one copy of X-hat, so more
- *                     CTAs share an SM (default for 16-lane MT19937-32
- *                     and 8-lane MT19937-64)
+ *                     CTAs share an SM (default for MT19937-32 with 8 or
+ *                     16 lanes and MT19937-64 with 4, 8 or 16 lanes)
  *   lanes_per_cta  lanes of the generator one CTA owns (chain form: M/lanes
  *                     CTAs share a generator; unit launches use one CTA)
  *   threads        CTA size

@@ -59,6 +59,7 @@ constexpr KernelCfg kKernelCfgs[] = {
     {VMT_MT19937_32, 16, kChain, 16, 512, 16},
     {VMT_MT19937_32, 16, kChain, 8, 128, 16},
     {VMT_MT19937_32, 16, kChain, 8, 256, 8},
+    {VMT_MT19937_32, 8, kInPlace, 8, 256, 16},
     {VMT_MT19937_32, 8, kPhase, 8, 256, 16},
     {VMT_MT19937_32, 8, kPhase, 8, 512, 16},
     {VMT_MT19937_32, 8, kChain, 8, 256, 16},
@@ -66,17 +67,18 @@ constexpr KernelCfg kKernelCfgs[] = {
     {VMT_MT19937_32, 4, kPhase, 4, 256, 16},
     {VMT_MT19937_32, 4, kChain, 4, 128, 16},
     // V-MT19937-64
+    {VMT_MT19937_64, 16, kInPlace, 16, 256, 16},
     {VMT_MT19937_64, 16, kPhase, 16, 512, 16},
     {VMT_MT19937_64, 16, kPhase, 16, 1024, 16},
     {VMT_MT19937_64, 16, kChain, 4, 160, 16},
     {VMT_MT19937_64, 16, kChain, 8, 320, 16},
-    {VMT_MT19937_64, 16, kInPlace, 16, 256, 16},
     {VMT_MT19937_64, 8, kInPlace, 8, 256, 16},
     {VMT_MT19937_64, 8, kPhase, 8, 256, 16},
     {VMT_MT19937_64, 8, kPhase, 8, 512, 16},
     {VMT_MT19937_64, 8, kChain, 4, 160, 16},
     {VMT_MT19937_64, 8, kChain, 8, 320, 16},
     {VMT_MT19937_64, 8, kChain, 4, 160, 8},
+    {VMT_MT19937_64, 4, kInPlace, 4, 256, 16},
     {VMT_MT19937_64, 4, kPhase, 4, 256, 16},
     {VMT_MT19937_64, 4, kChain, 4, 160, 16},
 };

@@ -12,7 +12,9 @@ cudaError_t launch_generate_mt32(int lanes, int t, bool ip, bool m1, const GenAr
     case 1: return launch_mt<MT32, 1, 1, 256>(a, s);
     case 2: return launch_mt<MT32, 2, 2, 256>(a, s);
     case 4: return launch_mt<MT32, 4, 4, 256>(a, s);
-    case 8: return t == 512 ? launch_mt<MT32, 8, 4, 512>(a, s) : launch_mt<MT32, 8, 4, 256>(a, s);
+    case 8:
+        if (ip) return launch_mt<MT32, 8, 4, 256, true>(a, s);
+        return t == 512 ? launch_mt<MT32, 8, 4, 512>(a, s) : launch_mt<MT32, 8, 4, 256>(a, s);
     case 16:
         if (ip) return launch_mt<MT32, 16, 4, 256, true>(a, s);
         return t == 1024 ? launch_mt<MT32, 16, 4, 1024>(a, s) : launch_mt<MT32, 16, 4, 512>(a, s);

@@ -15,7 +15,7 @@ cudaError_t launch_generate_mt64(int lanes, int t, bool ip, bool m1, const GenAr
     switch (lanes) {
     case 1: return launch_mt<MT64, 1, 1, 256>(a, s);
     case 2: return launch_mt<MT64, 2, 2, 256>(a, s);
-    case 4: return launch_mt<MT64, 4, 2, 256>(a, s);
+    case 4: return ip ? launch_mt<MT64, 4, 2, 256, true>(a, s) : launch_mt<MT64, 4, 2, 256>(a, s);
     case 8:
         if (ip) return launch_mt<MT64, 8, 2, 256, true>(a, s);
         return t == 512 ? launch_mt<MT64, 8, 2, 512>(a, s) : launch_mt<MT64, 8, 2, 256>(a, s);
